@@ -1,0 +1,167 @@
+"""CPU oracle for breadth-first search -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  The GPU library never calls it and shares no
+code with it (the only common module is ``graphgen``, which makes inputs).
+
+* ``bfs(off, col, root)`` -- serial FIFO-queue BFS (Algorithm 1 run on one
+  thread; ``bfs_oracle.c``).  Returns int32 ``dist`` (-1 = unreachable,
+  Section "Preliminaries": d = infinity), one valid int32 ``parent``, and
+  an info dict (levels, per-level vertex counts, scanned entries m_c).
+* ``bfs_multi(off, col, roots)`` -- one independent BFS per root, k x n.
+* ``check_tree(off, col, root, dist, parent)`` -- Graph500-style checks of a
+  BFS result that do not depend on which of several valid parents was
+  chosen (used to accept GPU parents).
+
+Pins: ``tests/test_oracle_pins.py`` checks this oracle against Floyd-Warshall
+brute force, closed-form distances, scipy's breadth-first search, and
+union-find components.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bfs_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False, src: str | None = None, out: str | None = None) -> str:
+    """Compile the oracle with plain gcc (no OpenMP, no vectorisation flags)."""
+    src = src or _SRC
+    out = out or _LIB_PATH
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, out)
+    return out
+
+
+def load(path: str | None = None):
+    """Load the oracle library (the default build, or another compiled copy)."""
+    global _lib
+    if path is None:
+        with _lock:
+            if _lib is None:
+                _lib = _bind(ctypes.CDLL(build()))
+        return _lib
+    return _bind(ctypes.CDLL(path))
+
+
+def _bind(lib):
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    lib.oracle_bfs.argtypes = [ctypes.c_int64, i64p, i32p, ctypes.c_int64, i32p, i32p, i64p,
+                               ctypes.c_int64, i64p]
+    lib.oracle_bfs.restype = ctypes.c_int64
+    lib.oracle_bfs_multi.argtypes = [ctypes.c_int64, i64p, i32p, i64p, ctypes.c_int64, i32p, i64p]
+    lib.oracle_bfs_multi.restype = ctypes.c_int64
+    return lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def _csr(off, col):
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    if col.size == 0:
+        col = np.zeros(1, dtype=np.int32)
+    return off, col
+
+
+def bfs(off, col, root, lib=None):
+    """Serial BFS from ``root``: (dist int32[n], parent int32[n], info)."""
+    lib = lib or load()
+    off, col = _csr(off, col)
+    n = len(off) - 1
+    if not (0 <= root < n):
+        raise ValueError("root out of range")
+    dist = np.empty(n, dtype=np.int32)
+    parent = np.empty(n, dtype=np.int32)
+    max_levels = n + 1
+    levels = np.zeros(max_levels, dtype=np.int64)
+    scanned = np.zeros(1, dtype=np.int64)
+    nl = lib.oracle_bfs(n, _p(off, ctypes.c_int64), _p(col, ctypes.c_int32), int(root),
+                        _p(dist, ctypes.c_int32), _p(parent, ctypes.c_int32),
+                        _p(levels, ctypes.c_int64), max_levels, _p(scanned, ctypes.c_int64))
+    if nl < 0:
+        raise RuntimeError(f"oracle_bfs failed ({nl})")
+    info = {"levels": int(nl), "level_sizes": levels[:nl].copy(), "edges_scanned": int(scanned[0]),
+            "reached": int(np.count_nonzero(dist >= 0))}
+    return dist, parent, info
+
+
+def bfs_multi(off, col, roots, lib=None):
+    """One independent BFS per root: (dist int32[k][n], scanned int64[k])."""
+    lib = lib or load()
+    off, col = _csr(off, col)
+    n = len(off) - 1
+    roots = np.ascontiguousarray(roots, dtype=np.int64)
+    k = len(roots)
+    dist = np.empty((k, n), dtype=np.int32)
+    scanned = np.zeros(max(k, 1), dtype=np.int64)
+    rc = lib.oracle_bfs_multi(n, _p(off, ctypes.c_int64), _p(col, ctypes.c_int32),
+                              _p(roots, ctypes.c_int64), k, _p(dist, ctypes.c_int32),
+                              _p(scanned, ctypes.c_int64))
+    if rc < 0:
+        raise RuntimeError(f"oracle_bfs_multi failed ({rc})")
+    return dist, scanned[:k]
+
+
+def check_tree(off, col, root, dist, parent, undirected=True):
+    """Graph500-style validation of a BFS result; returns a list of problems
+    (empty when valid).  Checks: dist[root] = 0 and parent[root] = root; every
+    reached v != root has a parent p with an edge p -> v and dist[p] =
+    dist[v] - 1 (so following parents reaches the root in dist[v] steps);
+    unreached vertices have parent -1; on undirected graphs every edge joins
+    two reached or two unreached vertices and |dist[u] - dist[v]| <= 1."""
+    off = np.asarray(off, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int32)
+    dist = np.asarray(dist, dtype=np.int64)
+    parent = np.asarray(parent, dtype=np.int64)
+    n = len(off) - 1
+    bad = []
+    if dist[root] != 0:
+        bad.append("dist[root] != 0")
+    if parent[root] != root:
+        bad.append("parent[root] != root")
+    reached = dist >= 0
+    unreached_with_parent = np.nonzero(~reached & (parent != -1))[0]
+    if unreached_with_parent.size:
+        bad.append(f"{unreached_with_parent.size} unreached vertices have a parent")
+    others = np.nonzero(reached)[0]
+    others = others[others != root]
+    if others.size:
+        p = parent[others]
+        if np.any((p < 0) | (p >= n)):
+            bad.append("reached vertex with parent out of range")
+            return bad
+        if np.any(dist[p] != dist[others] - 1):
+            bad.append("parent not one level closer to the root")
+        # edge p -> v must exist: binary search in p's sorted-or-not row
+        src = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
+        key_edges = src * n + col.astype(np.int64)
+        key_edges.sort()
+        key_par = p * n + others
+        pos = np.searchsorted(key_edges, key_par)
+        pos = np.minimum(pos, max(len(key_edges) - 1, 0))
+        if len(key_edges) == 0 or np.any(key_edges[pos] != key_par):
+            bad.append("parent is not adjacent to the vertex")
+    if undirected and len(col):
+        src = np.repeat(np.arange(n, dtype=np.int64), np.diff(off))
+        du, dv = dist[src], dist[col]
+        if np.any((du >= 0) != (dv >= 0)):
+            bad.append("edge between reached and unreached vertex")
+        both = (du >= 0) & (dv >= 0)
+        if np.any(np.abs(du[both] - dv[both]) > 1):
+            bad.append("edge spans more than one level")
+    return bad
