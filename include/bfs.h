@@ -1,0 +1,214 @@
+/*
+ * bfs.h -- C ABI of the GB300 breadth-first-search library (libbfs.so).
+ *
+ * The library runs the per-GPU top-down level step of ButterFly BFS
+ * (Green, "ButterFly BFS - An Efficient Communication Pattern for Multi
+ * Node Traversals", arXiv 2103.13577): Algorithm 2 Phase 1 with one compute
+ * node, which is Algorithm 1 with an atomic enqueue -- expand every frontier
+ * vertex's adjacency list, claim each unvisited neighbour exactly once,
+ * write its distance (level + 1), and build the next frontier.  On top of
+ * that it offers 64-root batched traversal and a query server.
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are CSR: row_off int64[n+1] (row_off[0] = 0, non-decreasing,
+ *     row_off[n] = nnz) and col int32[nnz] with 0 <= col[e] < n.  Edge
+ *     (v, col[e]) for row_off[v] <= e < row_off[v+1] is directed v -> col[e]
+ *     (Section "Preliminaries": an undirected graph stores both directions).
+ *     Duplicates and self-loops are allowed and harmless; nothing is repaired.
+ *   - Distances are int32 (int8 where a flag says so): d[root] = 0, d[v] =
+ *     hops of a shortest path root -> v, and -1 for "infinity" (no path).
+ *   - Parents: parent[root] = root, -1 when unreached, otherwise some vertex
+ *     p with an edge p -> v and d[p] = d[v] - 1.  When several such p exist,
+ *     which one is returned is unspecified.
+ *   - Streams are cudaStream_t values passed as void* (NULL = legacy default
+ *     stream).  A call with device outputs only enqueues work and returns;
+ *     a call with any host buffer also waits for that stream.
+ *   - Every call returns a bfs_status; nothing throws across the ABI.
+ *     bfs_last_error() gives a message for the calling thread's last failure.
+ *   - Pointers stay owned by the caller unless a function says otherwise.
+ */
+#ifndef BFS_H
+#define BFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t bfs_status;
+
+#define BFS_OK                  0
+#define BFS_PENDING             1   /* bfs_poll: query not finished yet */
+#define BFS_ERR_INVALID_ARG    -1   /* null pointer, bad size or flag */
+#define BFS_ERR_INVALID_GRAPH  -2   /* CSR fails the checks listed above */
+#define BFS_ERR_ROOT_RANGE     -3   /* root < 0 or root >= n */
+#define BFS_ERR_NO_MEMORY      -4   /* device allocation (or arena) exhausted */
+#define BFS_ERR_BUDGET         -5   /* server: query can never fit the budget */
+#define BFS_ERR_DEPTH_OVERFLOW -6   /* int8 distances: a level above 126 */
+#define BFS_ERR_TIMEOUT        -7   /* a bounded device-side wait gave up */
+#define BFS_ERR_CUDA           -8   /* CUDA runtime error (message has it) */
+#define BFS_ERR_UNSUPPORTED    -9   /* graph too large for the encoding */
+#define BFS_ERR_CANCELLED     -10   /* server shut down before the query ran */
+#define BFS_ERR_NOT_FOUND     -11   /* unknown ticket or graph id */
+
+typedef struct bfs_context bfs_context;
+typedef struct bfs_graph bfs_graph;
+typedef struct bfs_server bfs_server;
+typedef int64_t bfs_ticket;
+
+/* ---- flags ------------------------------------------------------------ */
+/* bfs_graph_upload */
+#define BFS_UPLOAD_DEVICE_PTRS  0x1u  /* row_off/col are device pointers */
+#define BFS_UPLOAD_NO_RELABEL   0x2u  /* keep the caller's vertex order on device */
+/* bfs_run / bfs_run_batch */
+#define BFS_OUT_HOST            0x1u  /* outputs are host pointers (copied back, call waits) */
+#define BFS_DIST_INT8           0x2u  /* bfs_run_batch: int8 distances (levels <= 126) */
+#define BFS_HOST_LOOP           0x4u  /* one kernel launch per level, host reads the frontier
+                                         size between levels (no device-side loop) */
+
+/* ---- context ------------------------------------------------------------
+ * A context binds the library to one CUDA device.  arena (device pointer,
+ * may be NULL) and arena_bytes let the caller hand over one pre-allocated
+ * device buffer (for instance a torch uint8 tensor); every device buffer the
+ * library needs is then carved from it and nothing else is allocated.  With
+ * arena == NULL the library calls cudaMalloc itself.  The arena stays owned
+ * by the caller and must outlive the context. */
+bfs_status bfs_context_create(int device, void* arena, size_t arena_bytes, bfs_context** out);
+bfs_status bfs_context_destroy(bfs_context* ctx);
+/* bytes of device memory the context currently holds (arena or cudaMalloc) */
+bfs_status bfs_context_memory(const bfs_context* ctx, size_t* used, size_t* capacity);
+
+/* ---- graphs ---------------------------------------------------------------
+ * bfs_graph_upload copies the CSR to the device (host or device source per
+ * flags), checks it (BFS_ERR_INVALID_GRAPH), and sizes every per-traversal
+ * buffer once (the paper's tight memory bound: buffers are allocated in
+ * advance and reused by every level, Section "Fanout & Trade-offs" and
+ * contribution 4).  Unless BFS_UPLOAD_NO_RELABEL is given, vertices are
+ * renumbered on the device by decreasing degree; results are always
+ * returned in the caller's numbering.  The caller may free its arrays when
+ * the call returns.  stream orders the copies. */
+bfs_status bfs_graph_upload(bfs_context* ctx, const int64_t* row_off, const int32_t* col,
+                            int64_t n, int64_t nnz, uint32_t flags, void* stream,
+                            bfs_graph** out);
+bfs_status bfs_graph_free(bfs_graph* g);
+
+typedef struct bfs_graph_info {
+    int64_t n;              /* vertices */
+    int64_t nnz;            /* directed adjacency entries */
+    int64_t max_degree;
+    int32_t t_small;        /* degree bins: deg < t_small -> warp-gather bin */
+    int32_t t_large;        /* deg >= t_large -> CTA bin, otherwise warp bin */
+    int32_t chunk_warp;     /* edges per warp work item (warp bin) */
+    int32_t chunk_cta;      /* edges per CTA work item (CTA bin) */
+    int32_t relabelled;     /* 1 when the device copy is degree-ordered */
+    int32_t grid_blocks;    /* persistent grid size used by the device loop */
+    size_t device_bytes;    /* device memory held by the graph and its buffers */
+} bfs_graph_info;
+bfs_status bfs_graph_get_info(const bfs_graph* g, bfs_graph_info* out);
+
+/* Degree-bin thresholds and work-item sizes (the autotuner's knobs).
+ * t_small >= 1, t_large > t_small, chunk_warp a multiple of 128,
+ * chunk_cta a multiple of 1024.  Reallocates the per-traversal buffers;
+ * must not be called while a traversal on g is in flight. */
+bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
+                              int32_t chunk_warp, int32_t chunk_cta);
+
+/* Per-graph tuning options (bfs_graph_set_option):
+ *   BFS_OPT_WARP_AGGREGATE   0/1: lanes of a warp that claim vertices in the
+ *                            same 32-bit visited word merge their bits and
+ *                            issue one atomicOr (default 0).
+ *   BFS_OPT_TIMEOUT_NS       limit of every device-side grid-barrier wait,
+ *                            in ns (default 2e9); expiry ends the traversal
+ *                            with BFS_ERR_TIMEOUT. */
+#define BFS_OPT_WARP_AGGREGATE  1
+#define BFS_OPT_TIMEOUT_NS      2
+bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value);
+
+/* ---- single-source traversal ----------------------------------------------
+ * Algorithm 1 / Algorithm 2 Phase 1 (one compute node) from `root` (caller
+ * numbering).  dist: int32[n]; parent: int32[n] or NULL.  Device pointers by
+ * default (stream-ordered, returns after enqueueing); with BFS_OUT_HOST they
+ * are host pointers and the call waits for completion.  Concurrent calls on
+ * one graph must use the same stream (the graph's traversal buffers are
+ * shared).  Errors detected on the device (timeout) are reported by the
+ * next call that synchronises (BFS_OUT_HOST, bfs_graph_sync). */
+bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* dist, int32_t* parent, void* stream,
+                   uint32_t flags);
+
+typedef struct bfs_run_stats {
+    int64_t levels;         /* number of non-empty frontiers (max dist + 1) */
+    int64_t reached;        /* vertices with dist >= 0 */
+    int64_t edges_scanned;  /* adjacency entries expanded (m_c, TEPS numerator) */
+    int32_t status;         /* device-side status of the last traversal */
+} bfs_run_stats;
+/* Waits for `stream`, then reports the last traversal run on g. */
+bfs_status bfs_graph_sync(bfs_graph* g, void* stream, bfs_run_stats* stats);
+
+/* ---- batched traversal ------------------------------------------------------
+ * k independent traversals (1 <= k <= 64) from roots[0..k) (host array,
+ * caller numbering; duplicates allowed) in one persistent launch, each vertex
+ * carrying a 64-bit source-lane bitset.  dist: k rows of n (row i = the
+ * distances from roots[i]), int32 by default or int8 with BFS_DIST_INT8
+ * (-1 = unreached; a level above 126 makes the call fail with
+ * BFS_ERR_DEPTH_OVERFLOW).  Device or host pointer as for bfs_run.
+ * Each row equals bfs_run(roots[i]). */
+bfs_status bfs_run_batch(bfs_graph* g, const int32_t* roots, int32_t k, void* dist,
+                         void* stream, uint32_t flags);
+/* Waits for `stream`, then reports the last batched traversal run on g:
+ * levels = deepest lane's levels, reached = sum over lanes of reached
+ * vertices, edges_scanned = sum over lanes of m_c (the batch's TEPS
+ * numerator). */
+bfs_status bfs_batch_sync(bfs_graph* g, void* stream, bfs_run_stats* stats);
+
+/* ---- serving ---------------------------------------------------------------
+ * A server keeps graphs resident and runs single-root queries as they
+ * arrive.  Queries on the same graph that are waiting together are packed
+ * into one batched launch of up to 64 lanes; launches run on num_streams
+ * CUDA streams so work from different graphs overlaps on the device.  A
+ * launch is admitted only while the device memory of all launches in
+ * flight stays within memory_budget bytes; queries that do not fit wait.
+ * A query whose smallest launch alone exceeds the budget fails with
+ * BFS_ERR_BUDGET.  dist_out (host, int32[n]) is written when the query
+ * completes; the pointer must stay valid until then. */
+bfs_status bfs_server_create(bfs_context* ctx, size_t memory_budget, int32_t num_streams,
+                             bfs_server** out);
+bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id);
+bfs_status bfs_submit(bfs_server* s, int32_t graph_id, int32_t root, int32_t* dist_out,
+                      bfs_ticket* ticket);
+/* BFS_PENDING while queued or running, BFS_OK once dist_out is written, or
+ * the query's error.  A finished ticket can be polled until it is released. */
+bfs_status bfs_poll(bfs_server* s, bfs_ticket ticket);
+/* Waits up to timeout_us (< 0 = no limit) for the ticket. */
+bfs_status bfs_wait(bfs_server* s, bfs_ticket ticket, int64_t timeout_us);
+/* Forget a finished ticket. */
+bfs_status bfs_release(bfs_server* s, bfs_ticket ticket);
+
+typedef struct bfs_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t launches;         /* batched launches issued */
+    int64_t lanes;            /* queries carried by those launches */
+    int64_t max_inflight_bytes;
+} bfs_server_stats;
+bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out);
+/* Stops the server; queued queries finish with BFS_ERR_CANCELLED. */
+bfs_status bfs_server_destroy(bfs_server* s);
+
+/* ---- diagnostics ------------------------------------------------------------ */
+const char* bfs_last_error(void);
+const char* bfs_status_string(bfs_status s);
+int32_t bfs_version(void);
+
+/* Fault-detection hook for tests: makes the next device-side grid barrier
+ * on g wait for an arrival that never comes, so the bounded wait (limit
+ * timeout_ns) expires and the traversal ends with BFS_ERR_TIMEOUT.  The
+ * kernel returns normally; the context stays usable.  timeout_ns = 0
+ * restores normal operation (default limit). */
+bfs_status bfs_debug_set_barrier_test(bfs_graph* g, int32_t stall, int64_t timeout_ns);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFS_H */

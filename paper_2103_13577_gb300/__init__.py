@@ -1,0 +1,60 @@
+"""GB300-native breadth-first search (ButterFly BFS per-GPU level step).
+
+Thin Python binding over the C ABI of ``libbfs.so`` (``include/bfs.h``):
+the functions below carry the C names and only marshal arguments (numpy
+arrays -> host pointers, torch CUDA tensors -> device pointers, torch
+streams -> cudaStream_t).  Every step of a traversal runs in the library's
+CUDA kernels; there is no CPU fallback -- loading fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+from ._lib import (  # noqa: F401
+    BFS_DIST_INT8,
+    BFS_ERR_BUDGET,
+    BFS_ERR_CANCELLED,
+    BFS_ERR_CUDA,
+    BFS_ERR_DEPTH_OVERFLOW,
+    BFS_ERR_INVALID_ARG,
+    BFS_ERR_INVALID_GRAPH,
+    BFS_ERR_NO_MEMORY,
+    BFS_ERR_NOT_FOUND,
+    BFS_ERR_ROOT_RANGE,
+    BFS_ERR_TIMEOUT,
+    BFS_ERR_UNSUPPORTED,
+    BFS_HOST_LOOP,
+    BFS_OPT_TIMEOUT_NS,
+    BFS_OPT_WARP_AGGREGATE,
+    BFS_OK,
+    BFS_OUT_HOST,
+    BFS_PENDING,
+    BFS_UPLOAD_DEVICE_PTRS,
+    BFS_UPLOAD_NO_RELABEL,
+    BfsError,
+    lib,
+    load,
+)
+from .api import (  # noqa: F401
+    Context,
+    Graph,
+    Server,
+    bfs_batch_sync,
+    bfs_context_create,
+    bfs_context_destroy,
+    bfs_graph_free,
+    bfs_graph_get_info,
+    bfs_graph_set_bins,
+    bfs_graph_set_option,
+    bfs_graph_sync,
+    bfs_graph_upload,
+    bfs_poll,
+    bfs_release,
+    bfs_run,
+    bfs_run_batch,
+    bfs_server_add_graph,
+    bfs_server_create,
+    bfs_server_destroy,
+    bfs_server_get_stats,
+    bfs_submit,
+    bfs_wait,
+)

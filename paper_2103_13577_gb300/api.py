@@ -1,0 +1,276 @@
+"""Argument marshalling for the C ABI (include/bfs.h).
+
+Functions carry the C names.  Buffers may be numpy arrays (host memory) or
+torch CUDA tensors (device memory); the ``BFS_OUT_HOST`` /
+``BFS_UPLOAD_DEVICE_PTRS`` flags follow from which kind is passed.  Streams
+may be a ``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None
+(torch's current stream when torch has initialised CUDA, else the legacy
+default stream).
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (BFS_DIST_INT8, BFS_OUT_HOST, BFS_UPLOAD_DEVICE_PTRS, GraphInfo, RunStats,
+                   ServerStats, check)
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _buf(x, dtype: np.dtype | None = None):
+    """(pointer, is_device) of a numpy array or torch tensor."""
+    if x is None:
+        return None, False
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and x.dtype != dtype:
+            raise TypeError(f"expected {np.dtype(dtype)}, got {x.dtype}")
+        return x.ctypes.data, False
+    if _is_torch(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None:
+            want = {np.dtype(np.int32): "torch.int32", np.dtype(np.int64): "torch.int64",
+                    np.dtype(np.int8): "torch.int8", np.dtype(np.uint8): "torch.uint8"}[np.dtype(dtype)]
+            if str(x.dtype) != want:
+                raise TypeError(f"expected {want}, got {x.dtype}")
+        return x.data_ptr(), x.is_cuda
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:  # pragma: no cover
+            pass
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------- functions
+
+def bfs_context_create(device: int = 0, arena=None) -> int:
+    ptr = ctypes.c_void_p()
+    a, nbytes = None, 0
+    if arena is not None:
+        a, is_dev = _buf(arena)
+        if not is_dev:
+            raise ValueError("arena must be device memory")
+        nbytes = arena.numel() * arena.element_size()
+    check(_lib.lib().bfs_context_create(device, a, nbytes, ctypes.byref(ptr)), "bfs_context_create")
+    return ptr.value
+
+
+def bfs_context_destroy(ctx: int) -> None:
+    check(_lib.lib().bfs_context_destroy(ctx), "bfs_context_destroy")
+
+
+def bfs_graph_upload(ctx: int, row_off, col, flags: int = 0, stream=None) -> int:
+    p_off, dev_off = _buf(row_off, np.int64)
+    p_col, dev_col = _buf(col, np.int32)
+    if dev_off != dev_col:
+        raise ValueError("row_off and col must both be host or both be device buffers")
+    if dev_off:
+        flags |= BFS_UPLOAD_DEVICE_PTRS
+    n = (row_off.shape[0] if hasattr(row_off, "shape") else len(row_off)) - 1
+    nnz = col.shape[0] if hasattr(col, "shape") else len(col)
+    out = ctypes.c_void_p()
+    check(_lib.lib().bfs_graph_upload(ctx, p_off, p_col if nnz else None, n, nnz, flags,
+                                      _stream(stream), ctypes.byref(out)), "bfs_graph_upload")
+    return out.value
+
+
+def bfs_graph_free(g: int) -> None:
+    check(_lib.lib().bfs_graph_free(g), "bfs_graph_free")
+
+
+def bfs_graph_get_info(g: int) -> dict:
+    info = GraphInfo()
+    check(_lib.lib().bfs_graph_get_info(g, ctypes.byref(info)), "bfs_graph_get_info")
+    return {f: getattr(info, f) for f, _ in GraphInfo._fields_}
+
+
+def bfs_graph_set_bins(g: int, t_small: int, t_large: int, chunk_warp: int, chunk_cta: int) -> None:
+    check(_lib.lib().bfs_graph_set_bins(g, t_small, t_large, chunk_warp, chunk_cta),
+          "bfs_graph_set_bins")
+
+
+def bfs_graph_set_option(g: int, option: int, value: int) -> None:
+    check(_lib.lib().bfs_graph_set_option(g, option, int(value)), "bfs_graph_set_option")
+
+
+def bfs_run(g: int, root: int, dist, parent=None, stream=None, flags: int = 0) -> None:
+    p_dist, dev = _buf(dist, np.int32)
+    p_par, dev_p = _buf(parent, np.int32)
+    if parent is not None and dev_p != dev:
+        raise ValueError("dist and parent must both be host or both be device buffers")
+    if not dev:
+        flags |= BFS_OUT_HOST
+    check(_lib.lib().bfs_run(g, int(root), p_dist, p_par, _stream(stream), flags), "bfs_run")
+
+
+def bfs_graph_sync(g: int, stream=None) -> dict:
+    st = RunStats()
+    check(_lib.lib().bfs_graph_sync(g, _stream(stream), ctypes.byref(st)), "bfs_graph_sync")
+    return {f: getattr(st, f) for f, _ in RunStats._fields_}
+
+
+def bfs_run_batch(g: int, roots, dist, stream=None, flags: int = 0) -> None:
+    roots = np.ascontiguousarray(roots, dtype=np.int32)
+    p_dist, dev = _buf(dist)
+    dt = dist.dtype if isinstance(dist, np.ndarray) else str(dist.dtype)
+    if str(dt) in ("int8", "torch.int8"):
+        flags |= BFS_DIST_INT8
+    elif str(dt) not in ("int32", "torch.int32"):
+        raise TypeError("dist must be int32 or int8")
+    if not dev:
+        flags |= BFS_OUT_HOST
+    check(_lib.lib().bfs_run_batch(g, roots.ctypes.data, len(roots), p_dist, _stream(stream), flags),
+          "bfs_run_batch")
+
+
+def bfs_batch_sync(g: int, stream=None) -> dict:
+    st = RunStats()
+    check(_lib.lib().bfs_batch_sync(g, _stream(stream), ctypes.byref(st)), "bfs_batch_sync")
+    return {f: getattr(st, f) for f, _ in RunStats._fields_}
+
+
+def bfs_server_create(ctx: int, memory_budget: int, num_streams: int = 4) -> int:
+    out = ctypes.c_void_p()
+    check(_lib.lib().bfs_server_create(ctx, memory_budget, num_streams, ctypes.byref(out)),
+          "bfs_server_create")
+    return out.value
+
+
+def bfs_server_add_graph(s: int, g: int) -> int:
+    gid = ctypes.c_int32()
+    check(_lib.lib().bfs_server_add_graph(s, g, ctypes.byref(gid)), "bfs_server_add_graph")
+    return gid.value
+
+
+def bfs_submit(s: int, graph_id: int, root: int, dist_out) -> int:
+    p, dev = _buf(dist_out, np.int32)
+    if dev:
+        raise ValueError("dist_out must be host memory")
+    t = ctypes.c_int64()
+    check(_lib.lib().bfs_submit(s, graph_id, int(root), p, ctypes.byref(t)), "bfs_submit")
+    return t.value
+
+
+def bfs_poll(s: int, ticket: int) -> int:
+    return check(_lib.lib().bfs_poll(s, ticket), "bfs_poll")
+
+
+def bfs_wait(s: int, ticket: int, timeout_us: int = -1) -> int:
+    return check(_lib.lib().bfs_wait(s, ticket, timeout_us), "bfs_wait")
+
+
+def bfs_release(s: int, ticket: int) -> None:
+    check(_lib.lib().bfs_release(s, ticket), "bfs_release")
+
+
+def bfs_server_get_stats(s: int) -> dict:
+    st = ServerStats()
+    check(_lib.lib().bfs_server_get_stats(s, ctypes.byref(st)), "bfs_server_get_stats")
+    return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+
+def bfs_server_destroy(s: int) -> None:
+    check(_lib.lib().bfs_server_destroy(s), "bfs_server_destroy")
+
+
+# ----------------------------------------------------- small conveniences
+
+class Context:
+    def __init__(self, device: int = 0, arena=None):
+        self._arena = arena
+        self.handle = bfs_context_create(device, arena)
+
+    def close(self):
+        if self.handle:
+            bfs_context_destroy(self.handle)
+            self.handle = None
+
+    def memory(self) -> tuple[int, int]:
+        used, cap = ctypes.c_size_t(), ctypes.c_size_t()
+        check(_lib.lib().bfs_context_memory(self.handle, ctypes.byref(used), ctypes.byref(cap)),
+              "bfs_context_memory")
+        return used.value, cap.value
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Graph:
+    def __init__(self, ctx: Context, row_off, col, flags: int = 0, stream=None):
+        self.ctx = ctx
+        self.handle = bfs_graph_upload(ctx.handle, row_off, col, flags, stream)
+        self.n = (row_off.shape[0] if hasattr(row_off, "shape") else len(row_off)) - 1
+
+    def info(self) -> dict:
+        return bfs_graph_get_info(self.handle)
+
+    def set_bins(self, t_small, t_large, chunk_warp, chunk_cta):
+        bfs_graph_set_bins(self.handle, t_small, t_large, chunk_warp, chunk_cta)
+
+    def set_option(self, option: int, value: int):
+        bfs_graph_set_option(self.handle, option, value)
+
+    def run(self, root, dist, parent=None, stream=None, flags=0):
+        bfs_run(self.handle, root, dist, parent, stream, flags)
+
+    def sync(self, stream=None) -> dict:
+        return bfs_graph_sync(self.handle, stream)
+
+    def run_batch(self, roots, dist, stream=None, flags=0):
+        bfs_run_batch(self.handle, roots, dist, stream, flags)
+
+    def batch_sync(self, stream=None) -> dict:
+        return bfs_batch_sync(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            bfs_graph_free(self.handle)
+            self.handle = None
+
+
+class Server:
+    def __init__(self, ctx: Context, memory_budget: int, num_streams: int = 4):
+        self.handle = bfs_server_create(ctx.handle, memory_budget, num_streams)
+
+    def add_graph(self, g: Graph) -> int:
+        return bfs_server_add_graph(self.handle, g.handle)
+
+    def submit(self, graph_id: int, root: int, dist_out) -> int:
+        return bfs_submit(self.handle, graph_id, root, dist_out)
+
+    def poll(self, ticket: int) -> int:
+        return bfs_poll(self.handle, ticket)
+
+    def wait(self, ticket: int, timeout_us: int = -1) -> int:
+        return bfs_wait(self.handle, ticket, timeout_us)
+
+    def release(self, ticket: int) -> None:
+        bfs_release(self.handle, ticket)
+
+    def stats(self) -> dict:
+        return bfs_server_get_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            bfs_server_destroy(self.handle)
+            self.handle = None

@@ -1,0 +1,93 @@
+// bfs_internal.h -- structures shared by the kernels and the host runtime.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace bfs {
+
+constexpr int kBlock = 256;               // threads per CTA of every traversal kernel
+constexpr int kWarps = kBlock / 32;
+constexpr int kBins = 3;                  // 0: warp-gather, 1: warp-per-vertex, 2: CTA chunks
+constexpr int kCountShift = 34;           // packed bin counter: (count << 34) | edges
+constexpr unsigned long long kEdgeMask = (1ull << kCountShift) - 1ull;
+constexpr int64_t kMaxVertices = (1ll << 30) - 1;    // count field holds 30 bits
+constexpr int64_t kMaxEdges = (1ll << kCountShift) - 1;
+
+// Device status codes (mirrors of BFS_ERR_* that the kernels can raise).
+enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevOverflow = 2, kDevDepth = 3 };
+
+// One slot of the per-level control block; three slots rotate by level so
+// that the slot being written (next frontier), the slot being read (current
+// frontier) and the slot being cleared never coincide.
+struct LevelCtl {
+    unsigned long long packed[kBins];  // per bin: (entries << 34) | sum of degrees
+    unsigned int work;                  // dynamic work-item counter of this level
+    unsigned int discovered;            // vertices claimed at this level (any degree)
+    unsigned long long new_lanes;       // batched: (vertex, lane) pairs discovered
+    unsigned long long pad[2];
+};
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int pad[30];
+};
+
+struct DevStats {
+    long long levels;
+    long long reached;
+    long long edges;
+    int status;       // sticky result of the launch (read by the host)
+    int max_level;
+    int abort;        // set with status; tells waiting CTAs to leave; cleared at kernel exit
+    int pad[3];
+};
+
+// Frontier queue of one bin (one of two ping-pong copies).
+struct BinQueue {
+    int32_t* v;            // vertex (device numbering)
+    int64_t* eoff;         // exclusive prefix of degrees inside the bin (bins 1, 2)
+    int32_t* chunk;        // first entry of each edge chunk (bins 1, 2)
+    uint64_t* mask;        // batched traversal: source-lane bitset of the entry
+    int64_t cap;           // entries
+    int64_t chunk_cap;     // chunk-start slots
+};
+
+struct TraversalParams {
+    // graph (device numbering)
+    int64_t n;
+    const int64_t* off;
+    const int32_t* col;
+    const int32_t* new2old;   // device -> caller numbering (nullptr: identity)
+    const int32_t* old2new;   // caller -> device numbering (nullptr: identity)
+    // degree bins
+    int32_t t_small;
+    int32_t t_large;
+    int32_t chunk_warp;
+    int32_t chunk_cta;
+    // workspace
+    uint32_t* visited;        // plain: 1 bit per vertex
+    BinQueue q[2][kBins];
+    LevelCtl* ctl;            // [3]
+    GridBarrier* bar;
+    DevStats* stats;
+    // batched traversal state
+    uint64_t* lane_visited;   // [n]
+    uint64_t* lane_next;      // [n]
+    int32_t nlanes;
+    int32_t dist_int8;
+    int32_t roots[64];        // caller numbering, [nlanes]
+    // outputs (caller numbering)
+    int32_t* dist;            // plain: [n]; batched: [nlanes][n] (int32 or int8)
+    int32_t* parent;          // plain only, nullable
+    int32_t root_caller;      // plain: caller numbering
+    // control
+    int32_t level;            // host-loop mode: the level this launch runs
+    int32_t phase;            // host-loop mode: 0 init, 1 seed, 2 level (batched: 3 sweep)
+    long long timeout_ns;
+    int32_t debug_stall;
+    int32_t use_match_any;    // warp-aggregated atomicOr on the visited bitmap
+};
+
+}  // namespace bfs

@@ -1,0 +1,804 @@
+// bfs_kernels.cu -- the top-down level step on sm_103a.
+//
+// Algorithm 2 Phase 1 with one compute node (= Algorithm 1 with an atomic
+// enqueue): every vertex v of the current frontier scans adj(v); each
+// neighbour u whose distance is still infinity is claimed by exactly one
+// thread (the claim is an atomicOr on the visited bitmap; Algorithm 2 gates
+// the distance write on the success of the atomic enqueue), which writes
+// d[u] = level + 1 and appends u to the next frontier.  When the frontier is
+// empty the traversal ends (the While loop of Algorithm 1).
+//
+// GB300 design:
+//  * The whole level loop runs inside one cooperative persistent launch
+//    (grid = resident CTAs of all 152 SMs) separated by a grid barrier
+//    whose wait is bounded by %globaltimer, so no per-level host round trip.
+//  * Load balancing replaces the paper's Logarithmic Radix Binning (one
+//    kernel per log2-degree bin, Section "Load Balanced Traversals Per
+//    compute-node") with three degree bins written while the next frontier
+//    is built: deg < t_small (one lane per vertex, edges spread over the warp
+//    by a scan), t_small <= deg < t_large (one warp per vertex, 128-bit
+//    column loads) and deg >= t_large (one CTA per chunk of chunk_cta edges;
+//    heavy vertices span many CTAs).  Each bin counter packs (entries << 34 |
+//    edge prefix) so that one 64-bit atomicAdd per warp reserves queue slots
+//    and edge ranges at once; warp and CTA work items are fixed-size edge
+//    chunks, located through a chunk-start table filled at enqueue time.
+//  * The batched traversal carries a 64-bit source-lane set per vertex:
+//    phase A ORs the frontier lanes into next[u], phase B (a sweep) turns the
+//    lanes that are new into distances and the next frontier.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "bfs_internal.h"
+
+namespace bfs {
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ unsigned lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
+    return __ldcg(p);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T y = __shfl_up_sync(FULL_MASK, x, d);
+        if (lane >= (unsigned)d) x += y;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void raise_status(const TraversalParams& P, int code) {
+    atomicCAS(&P.stats->status, 0, code);
+}
+
+// ------------------------------------------------------------ grid barrier
+// All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA
+// arrives on a counter; the last arrival resets it and bumps a generation
+// word that the others poll with acquire loads.  The poll gives up after
+// timeout_ns of %globaltimer, records kDevTimeout and returns false; it also
+// returns false as soon as another CTA has recorded a failure.
+__device__ bool grid_barrier(const TraversalParams& P) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        GridBarrier* B = P.bar;
+        int ok = 1;
+        const unsigned g = ld_acquire_u32(&B->gen);
+        __threadfence();
+        const unsigned target = gridDim.x + (P.debug_stall ? 1u : 0u);
+        const unsigned arrived = atomicAdd(&B->count, 1u) + 1u;
+        if (arrived == target) {
+            atomicExch(&B->count, 0u);
+            __threadfence();
+            st_release_u32(&B->gen, g + 1u);
+        } else {
+            const unsigned long long t0 = global_timer_ns();
+            while (ld_acquire_u32(&B->gen) == g) {
+                if (ld_volatile_i32(&P.stats->abort) != 0) { ok = 0; break; }
+                if (global_timer_ns() - t0 > (unsigned long long)P.timeout_ns) {
+                    raise_status(P, kDevTimeout);
+                    atomicExch(&P.stats->abort, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        if (ld_volatile_i32(&P.stats->abort) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Last CTA to leave a persistent launch clears the barrier and abort flag,
+// so the next launch starts clean even after a timed-out wait.
+__device__ void kernel_exit(const TraversalParams& P) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(&P.bar->pad[0], 1u) + 1u;
+        if (done == gridDim.x) {
+            atomicExch(&P.bar->count, 0u);
+            atomicExch(&P.bar->pad[0], 0u);
+            atomicExch(&P.stats->abort, 0);
+            __threadfence();
+        }
+    }
+}
+
+// --------------------------------------------------------------- enqueue
+// Warp-collective: every lane calls it; lanes with ok append (u, deg, mask)
+// to the degree bin of deg in the next frontier.  One 64-bit atomicAdd per
+// bin and warp reserves both the queue slots and the edge range.
+template <bool kBatch>
+__device__ __forceinline__ void enqueue_binned(const TraversalParams& P, bool ok, int32_t u,
+                                               long long deg, uint64_t mask, int nxt,
+                                               int nslot) {
+    ok = ok && deg > 0;  // nothing to expand from a vertex without out-edges
+    const int bin = deg < P.t_small ? 0 : (deg < P.t_large ? 1 : 2);
+    const unsigned lane = lane_id();
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        const bool mine = ok && bin == b;
+        const unsigned m = __ballot_sync(FULL_MASK, mine);
+        if (m == 0u) continue;
+        const long long d = mine ? deg : 0ll;
+        const long long incl = warp_incl_scan(d);
+        const long long tot = __shfl_sync(FULL_MASK, incl, 31);
+        unsigned long long basep = 0ull;
+        if (lane == 0)
+            basep = atomicAdd(&P.ctl[nslot].packed[b],
+                              ((unsigned long long)__popc(m) << kCountShift) +
+                                  (unsigned long long)tot);
+        basep = __shfl_sync(FULL_MASK, basep, 0);
+        if (mine) {
+            const BinQueue& Q = P.q[nxt][b];
+            const long long pos = (long long)(basep >> kCountShift) + __popc(m & lanemask_lt());
+            const long long eo = (long long)(basep & kEdgeMask) + incl - d;
+            if (pos < Q.cap) {
+                Q.v[pos] = u;
+                if (kBatch) Q.mask[pos] = mask;
+                if (b > 0) {
+                    Q.eoff[pos] = eo;
+                    const long long C = (b == 1) ? P.chunk_warp : P.chunk_cta;
+                    for (long long c = (eo + C - 1) / C; c * C < eo + d; ++c) {
+                        if (c < Q.chunk_cap) Q.chunk[c] = (int32_t)pos;
+                        else raise_status(P, kDevOverflow);
+                    }
+                }
+            } else {
+                raise_status(P, kDevOverflow);
+            }
+        }
+    }
+}
+
+// ----------------------------------------------------------------- visits
+// Plain traversal: claim u through the visited bitmap.  Warp-collective.
+__device__ __forceinline__ void visit_plain(const TraversalParams& P, bool valid, int32_t u,
+                                            int32_t v, int level, int nxt, int nslot) {
+    const unsigned lane = lane_id();
+    bool win = false;
+    uint32_t* wp = P.visited + (valid ? (u >> 5) : 0);
+    const uint32_t bit = 1u << (u & 31);
+    bool need = false;
+    if (valid) need = (*wp & bit) == 0u;  // may be stale: bits only go 0 -> 1
+    if (P.use_match_any) {
+        const unsigned needm = __ballot_sync(FULL_MASK, need);
+        if (need) {
+            const unsigned peers = __match_any_sync(needm, u >> 5);
+            const uint32_t bits = __reduce_or_sync(peers, bit);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0u;
+            if ((int)lane == leader) old = atomicOr(wp, bits);
+            old = __shfl_sync(peers, old, leader);
+            const unsigned same = __match_any_sync(peers, u);
+            win = ((old & bit) == 0u) && ((int)lane == __ffs(same) - 1);
+        }
+    } else if (need) {
+        win = (atomicOr(wp, bit) & bit) == 0u;
+    }
+    const unsigned winm = __ballot_sync(FULL_MASK, win);
+    if (winm == 0u) return;
+    long long deg = 0;
+    if (win) {
+        const int32_t cu = P.new2old ? __ldg(P.new2old + u) : u;
+        const int32_t cv = P.new2old ? __ldg(P.new2old + v) : v;
+        P.dist[cu] = level + 1;
+        if (P.parent) P.parent[cu] = cv;
+        const long long b0 = __ldg(P.off + u);
+        deg = __ldg(P.off + u + 1) - b0;
+    }
+    if (lane == 0) atomicAdd(&P.ctl[nslot].discovered, (unsigned)__popc(winm));
+    enqueue_binned<false>(P, win, u, deg, 0ull, nxt, nslot);
+}
+
+// Batched traversal, phase A: OR the entry's lanes that u has not seen into
+// next[u].  visited only changes in phase B, so a cached value is safe as a
+// filter.  Warp-collective (for symmetry with visit_plain; no warp ops).
+__device__ __forceinline__ void visit_batch(const TraversalParams& P, bool valid, int32_t u,
+                                            uint64_t mask) {
+    if (!valid) return;
+    const uint64_t m = mask & ~P.lane_visited[u];
+    if (m == 0ull) return;
+    unsigned long long* np = (unsigned long long*)(P.lane_next + u);
+    if ((m & ~*np) != 0ull) atomicOr(np, (unsigned long long)m);
+}
+
+template <bool kBatch>
+__device__ __forceinline__ void visit(const TraversalParams& P, bool valid, int32_t u, int32_t v,
+                                      uint64_t mask, int level, int nxt, int nslot) {
+    if (kBatch) visit_batch(P, valid, u, mask);
+    else visit_plain(P, valid, u, v, level, nxt, nslot);
+}
+
+// ------------------------------------------------------------ expansion
+// One column segment col[a, b) of vertex v, read by a group of warps with
+// 128-bit loads (start rounded down to 16 bytes; col is padded so the
+// rounded reads stay inside the allocation).  wbase/wstride give this
+// warp's first 256-entry block and the stride between its blocks.
+template <bool kBatch>
+__device__ __forceinline__ void expand_segment(const TraversalParams& P, long long a, long long b,
+                                               int32_t v, uint64_t mask, int level, int nxt,
+                                               int nslot, long long wbase, long long wstride) {
+    const unsigned lane = lane_id();
+    const long long a4 = a & ~3ll;
+    for (long long pw = a4 + wbase; pw < b; pw += wstride) {
+        const long long p0 = pw + 4 * lane;
+        const long long p1 = p0 + 128;
+        int4 x0 = make_int4(0, 0, 0, 0), x1 = make_int4(0, 0, 0, 0);
+        if (p0 < b) x0 = __ldcs(reinterpret_cast<const int4*>(P.col + p0));
+        if (p1 < b) x1 = __ldcs(reinterpret_cast<const int4*>(P.col + p1));
+        visit<kBatch>(P, p0 >= a && p0 < b, x0.x, v, mask, level, nxt, nslot);
+        visit<kBatch>(P, p0 + 1 >= a && p0 + 1 < b, x0.y, v, mask, level, nxt, nslot);
+        visit<kBatch>(P, p0 + 2 >= a && p0 + 2 < b, x0.z, v, mask, level, nxt, nslot);
+        visit<kBatch>(P, p0 + 3 >= a && p0 + 3 < b, x0.w, v, mask, level, nxt, nslot);
+        visit<kBatch>(P, p1 >= a && p1 < b, x1.x, v, mask, level, nxt, nslot);
+        visit<kBatch>(P, p1 + 1 >= a && p1 + 1 < b, x1.y, v, mask, level, nxt, nslot);
+        visit<kBatch>(P, p1 + 2 >= a && p1 + 2 < b, x1.z, v, mask, level, nxt, nslot);
+        visit<kBatch>(P, p1 + 3 >= a && p1 + 3 < b, x1.w, v, mask, level, nxt, nslot);
+    }
+}
+
+// Bin 0: 32 frontier vertices per warp, one per lane; their edges are laid
+// end to end by an exclusive scan and consumed 64 per round, lane l taking
+// edges l and l+32 and finding its owner vertex by a shuffle binary search.
+template <bool kBatch>
+__device__ void expand_small_group(const TraversalParams& P, int cur, long long grp,
+                                   long long cnt, int level, int nxt, int nslot) {
+    const BinQueue& Q = P.q[cur][0];
+    const unsigned lane = lane_id();
+    const long long i = grp * 32 + lane;
+    int32_t v = 0;
+    long long base = 0;
+    int deg = 0;
+    uint64_t mask = 0ull;
+    if (i < cnt) {
+        v = __ldcg(Q.v + i);
+        base = __ldg(P.off + v);
+        deg = (int)(__ldg(P.off + v + 1) - base);
+        if (kBatch) mask = __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + i);
+    }
+    const int incl = warp_incl_scan(deg);
+    const int excl = incl - deg;
+    const int total = __shfl_sync(FULL_MASK, incl, 31);
+    for (int e0 = 0; e0 < total; e0 += 64) {
+        int ea = e0 + (int)lane, eb = ea + 32;
+        int oa = 0, ob = 0;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            const int ca = oa + s, cb = ob + s;
+            const int xa = __shfl_sync(FULL_MASK, excl, ca & 31);
+            const int xb = __shfl_sync(FULL_MASK, excl, cb & 31);
+            if (xa <= ea) oa = ca;
+            if (xb <= eb) ob = cb;
+        }
+        const long long ba = __shfl_sync(FULL_MASK, base, oa);
+        const long long bb = __shfl_sync(FULL_MASK, base, ob);
+        const int xa = __shfl_sync(FULL_MASK, excl, oa);
+        const int xb = __shfl_sync(FULL_MASK, excl, ob);
+        const int32_t va = __shfl_sync(FULL_MASK, v, oa);
+        const int32_t vb = __shfl_sync(FULL_MASK, v, ob);
+        uint64_t ma = 0ull, mb = 0ull;
+        if (kBatch) {
+            ma = __shfl_sync(FULL_MASK, (unsigned long long)mask, oa);
+            mb = __shfl_sync(FULL_MASK, (unsigned long long)mask, ob);
+        }
+        const bool oka = ea < total, okb = eb < total;
+        const int32_t ua = oka ? __ldcs(P.col + ba + (ea - xa)) : 0;
+        const int32_t ub = okb ? __ldcs(P.col + bb + (eb - xb)) : 0;
+        visit<kBatch>(P, oka, ua, va, ma, level, nxt, nslot);
+        visit<kBatch>(P, okb, ub, vb, mb, level, nxt, nslot);
+    }
+}
+
+// Bin 1: one warp per chunk of chunk_warp edges; inside it, one vertex
+// segment at a time, the whole warp reading it with 128-bit loads.
+template <bool kBatch>
+__device__ void expand_warp_chunk(const TraversalParams& P, int cur, long long chunk,
+                                  long long cnt, long long E, int level, int nxt, int nslot) {
+    const BinQueue& Q = P.q[cur][1];
+    const unsigned lane = lane_id();
+    const long long cs = chunk * (long long)P.chunk_warp;
+    const long long ce = min(cs + (long long)P.chunk_warp, E);
+    long long i = __ldcg(Q.chunk + chunk);
+    for (;;) {
+        const long long ij = i + lane;
+        long long eo = 0x7fffffffffffffffll;
+        if (ij < cnt) eo = __ldcg(Q.eoff + ij);
+        const bool ok = eo < ce;
+        int32_t v = 0;
+        long long base = 0, end = 0;
+        uint64_t mask = 0ull;
+        if (ok) {
+            v = __ldcg(Q.v + ij);
+            base = __ldg(P.off + v);
+            end = __ldg(P.off + v + 1);
+            if (kBatch) mask = __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij);
+        }
+        const int nent = __popc(__ballot_sync(FULL_MASK, ok));
+        for (int k = 0; k < nent; ++k) {
+            const long long eok = __shfl_sync(FULL_MASK, eo, k);
+            const long long bk = __shfl_sync(FULL_MASK, base, k);
+            const long long ek = __shfl_sync(FULL_MASK, end, k);
+            const int32_t vk = __shfl_sync(FULL_MASK, v, k);
+            const uint64_t mk = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, k) : 0ull;
+            const long long lo = max(eok, cs), hi = min(eok + (ek - bk), ce);
+            expand_segment<kBatch>(P, bk + (lo - eok), bk + (hi - eok), vk, mk, level, nxt, nslot,
+                                   0, 256);
+        }
+        if (nent < 32) break;
+        i += 32;
+    }
+}
+
+// Bin 2: one CTA per chunk of chunk_cta edges (a heavy vertex spans many
+// chunks, hence many CTAs); the CTA's warps interleave over each segment.
+template <bool kBatch>
+__device__ void expand_cta_chunk(const TraversalParams& P, int cur, long long chunk,
+                                 long long cnt, long long E, int level, int nxt, int nslot) {
+    __shared__ long long s_eo[kBlock], s_base[kBlock], s_end[kBlock];
+    __shared__ int32_t s_v[kBlock];
+    __shared__ unsigned long long s_mask[kBlock];
+    const BinQueue& Q = P.q[cur][2];
+    const int warp = threadIdx.x >> 5;
+    const long long cs = chunk * (long long)P.chunk_cta;
+    const long long ce = min(cs + (long long)P.chunk_cta, E);
+    long long i = __ldcg(Q.chunk + chunk);
+    for (;;) {
+        const long long ij = i + threadIdx.x;
+        long long eo = 0x7fffffffffffffffll;
+        if (ij < cnt) eo = __ldcg(Q.eoff + ij);
+        const bool ok = eo < ce;
+        if (ok) {
+            const int32_t v = __ldcg(Q.v + ij);
+            s_v[threadIdx.x] = v;
+            s_eo[threadIdx.x] = eo;
+            s_base[threadIdx.x] = __ldg(P.off + v);
+            s_end[threadIdx.x] = __ldg(P.off + v + 1);
+            s_mask[threadIdx.x] =
+                kBatch ? __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij) : 0ull;
+        }
+        const int nent = __syncthreads_count(ok);
+        for (int k = 0; k < nent; ++k) {
+            const long long eok = s_eo[k], bk = s_base[k];
+            const long long lo = max(eok, cs), hi = min(eok + (s_end[k] - bk), ce);
+            expand_segment<kBatch>(P, bk + (lo - eok), bk + (hi - eok), s_v[k], s_mask[k], level,
+                                   nxt, nslot, (long long)warp * 256, 256ll * kWarps);
+        }
+        __syncthreads();
+        if (nent < kBlock) break;
+        i += kBlock;
+    }
+}
+
+struct LevelShape {
+    long long cnt[kBins], edges[kBins];
+    long long n_cta, chunks_warp, n_warp_items, groups_small, n_small_items, total;
+    unsigned discovered;
+};
+
+// Shape of level `level` (frontier in slot level % 3, queues level & 1).
+// Counts are clamped to the queue capacities so that a recorded overflow
+// can never turn into an out-of-bounds read.
+__device__ __forceinline__ LevelShape read_level(const TraversalParams& P, int level) {
+    LevelShape s;
+    const int slot = level % 3, cur = level & 1;
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        const unsigned long long p = ld_cg_u64(&P.ctl[slot].packed[b]);
+        s.cnt[b] = min((long long)(p >> kCountShift), (long long)P.q[cur][b].cap);
+        s.edges[b] = (long long)(p & kEdgeMask);
+    }
+    s.discovered = __ldcg(&P.ctl[slot].discovered);
+    s.n_cta = min((s.edges[2] + P.chunk_cta - 1) / P.chunk_cta, (long long)P.q[cur][2].chunk_cap);
+    s.chunks_warp =
+        min((s.edges[1] + P.chunk_warp - 1) / P.chunk_warp, (long long)P.q[cur][1].chunk_cap);
+    s.n_warp_items = (s.chunks_warp + kWarps - 1) / kWarps;
+    s.groups_small = (s.cnt[0] + 31) / 32;
+    s.n_small_items = (s.groups_small + kWarps - 1) / kWarps;
+    s.total = s.n_cta + s.n_warp_items + s.n_small_items;
+    return s;
+}
+
+// All CTAs pull work items of the level from one counter: first the CTA
+// chunks of bin 2 (largest first limits the tail), then warp items.
+template <bool kBatch>
+__device__ void expand_level(const TraversalParams& P, const LevelShape& S, int level) {
+    __shared__ long long s_item;
+    const int slot = level % 3, nslot = (level + 1) % 3;
+    const int cur = level & 1, nxt = cur ^ 1;
+    const int warp = threadIdx.x >> 5;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&P.ctl[slot].work, 1u);
+        __syncthreads();
+        const long long item = s_item;
+        __syncthreads();
+        if (item >= S.total) break;
+        if (item < S.n_cta) {
+            expand_cta_chunk<kBatch>(P, cur, item, S.cnt[2], S.edges[2], level, nxt, nslot);
+        } else if (item < S.n_cta + S.n_warp_items) {
+            const long long c = (item - S.n_cta) * kWarps + warp;
+            if (c < S.chunks_warp)
+                expand_warp_chunk<kBatch>(P, cur, c, S.cnt[1], S.edges[1], level, nxt, nslot);
+        } else {
+            const long long g = (item - S.n_cta - S.n_warp_items) * kWarps + warp;
+            if (g < S.groups_small)
+                expand_small_group<kBatch>(P, cur, g, S.cnt[0], level, nxt, nslot);
+        }
+    }
+}
+
+// ------------------------------------------------------------- init/seed
+// Byte-uniform fill (0x00 or 0xff patterns): scalar bytes up to a 16-byte
+// boundary, 16-byte stores for the body, scalar bytes for the tail.
+__device__ void fill_bytes(void* ptr, long long nbytes, unsigned char value, long long tid,
+                           long long nthreads) {
+    unsigned char* p = static_cast<unsigned char*>(ptr);
+    const long long head = min(nbytes, (long long)((16 - ((uintptr_t)p & 15)) & 15));
+    for (long long i = tid; i < head; i += nthreads) p[i] = value;
+    const long long nvec = (nbytes - head) / 16;
+    int4* pv = reinterpret_cast<int4*>(p + head);
+    const int w = (int)(value * 0x01010101u);
+    const int4 v4 = make_int4(w, w, w, w);
+    for (long long i = tid; i < nvec; i += nthreads) pv[i] = v4;
+    for (long long i = head + nvec * 16 + tid; i < nbytes; i += nthreads) p[i] = value;
+}
+
+__device__ void fill_u64(uint64_t* p, long long n, long long tid, long long nthreads) {
+    for (long long i = tid; i < n; i += nthreads) p[i] = 0ull;
+}
+
+__device__ void init_plain(const TraversalParams& P, long long tid, long long nthreads) {
+    if (blockIdx.x == 0 && threadIdx.x < 3 * (int)(sizeof(LevelCtl) / 8))
+        reinterpret_cast<unsigned long long*>(P.ctl)[threadIdx.x] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.stats->levels = 0;
+        P.stats->reached = 0;
+        P.stats->edges = 0;
+        P.stats->status = 0;
+        P.stats->max_level = 0;
+    }
+    const long long words = (P.n + 31) / 32;
+    fill_bytes(P.visited, words * 4, 0, tid, nthreads);
+    fill_bytes(P.dist, P.n * 4, 0xff, tid, nthreads);
+    if (P.parent) fill_bytes(P.parent, P.n * 4, 0xff, tid, nthreads);
+}
+
+__device__ void seed_plain(const TraversalParams& P) {
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const bool l0 = threadIdx.x == 0;
+    const int32_t root = P.old2new ? __ldg(P.old2new + P.root_caller) : P.root_caller;
+    long long deg = 0;
+    if (l0) {
+        P.visited[root >> 5] |= 1u << (root & 31);
+        P.dist[P.root_caller] = 0;
+        if (P.parent) P.parent[P.root_caller] = P.root_caller;
+        deg = __ldg(P.off + root + 1) - __ldg(P.off + root);
+        P.ctl[0].discovered = 1u;
+    }
+    enqueue_binned<false>(P, l0, root, deg, 0ull, 0, 0);
+}
+
+// Books the level that is about to be expanded; block 0, thread 0 only.
+__device__ void book_level(const TraversalParams& P, const LevelShape& S, int level) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    // clear the slot that the level after next will fill
+    unsigned long long* z = reinterpret_cast<unsigned long long*>(P.ctl + (level + 2) % 3);
+    for (int i = 0; i < (int)(sizeof(LevelCtl) / 8); ++i) z[i] = 0ull;
+    if (S.discovered > 0) {
+        P.stats->levels = level + 1;
+        P.stats->reached += S.discovered;
+    }
+    P.stats->edges += S.edges[0] + S.edges[1] + S.edges[2];
+}
+
+// --------------------------------------------------------- plain kernels
+__global__ void __launch_bounds__(kBlock)
+bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
+    const long long nthreads = (long long)gridDim.x * kBlock;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    init_plain(P, tid, nthreads);
+    if (grid_barrier(P)) {
+        seed_plain(P);
+        if (grid_barrier(P)) {
+            for (int level = 0;; ++level) {
+                const LevelShape S = read_level(P, level);
+                book_level(P, S, level);
+                if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) break;
+                expand_level<false>(P, S, level);
+                if (!grid_barrier(P)) break;
+            }
+        }
+    }
+    kernel_exit(P);
+}
+
+// Host-loop variant: one launch per phase / level, no grid barrier.
+__global__ void __launch_bounds__(kBlock)
+bfs_plain_step(const __grid_constant__ TraversalParams P) {
+    const long long nthreads = (long long)gridDim.x * kBlock;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (P.phase == 0) {
+        init_plain(P, tid, nthreads);
+    } else if (P.phase == 1) {
+        seed_plain(P);
+    } else {
+        const LevelShape S = read_level(P, P.level);
+        book_level(P, S, P.level);
+        if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) return;
+        expand_level<false>(P, S, P.level);
+    }
+}
+
+// ------------------------------------------------------- batched kernels
+__device__ void init_batch(const TraversalParams& P, long long tid, long long nthreads) {
+    if (blockIdx.x == 0 && threadIdx.x < 3 * (int)(sizeof(LevelCtl) / 8))
+        reinterpret_cast<unsigned long long*>(P.ctl)[threadIdx.x] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.stats->levels = 0;
+        P.stats->reached = 0;
+        P.stats->edges = 0;
+        P.stats->status = 0;
+        P.stats->max_level = 0;
+    }
+    fill_u64(P.lane_visited, P.n, tid, nthreads);
+    fill_u64(P.lane_next, P.n, tid, nthreads);
+    const long long total = (long long)P.nlanes * P.n;
+    fill_bytes(P.dist, total * (P.dist_int8 ? 1 : 4), 0xff, tid, nthreads);
+}
+
+__device__ __forceinline__ void write_lane_dist(const TraversalParams& P, int lane_idx,
+                                                int32_t cv, int value) {
+    const long long idx = (long long)lane_idx * P.n + cv;
+    if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)value;
+    else P.dist[idx] = value;
+}
+
+// One warp seeds all roots: duplicates share one queue entry whose mask
+// holds every lane with that root.
+__device__ void seed_batch(const TraversalParams& P) {
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const unsigned lane = lane_id();
+    long long reached = 0, edges = 0;
+    for (int base = 0; base < P.nlanes; base += 32) {
+        const int i = base + (int)lane;
+        bool first = false;
+        int32_t r = 0;
+        uint64_t mask = 0ull;
+        long long deg = 0;
+        if (i < P.nlanes) {
+            const int32_t cr = P.roots[i];
+            first = true;
+            for (int j = 0; j < P.nlanes; ++j) {
+                if (P.roots[j] == cr) {
+                    mask |= 1ull << j;
+                    if (j < i) first = false;
+                }
+            }
+            r = P.old2new ? __ldg(P.old2new + cr) : cr;
+            write_lane_dist(P, i, cr, 0);
+            deg = __ldg(P.off + r + 1) - __ldg(P.off + r);
+            if (first) {
+                P.lane_visited[r] = mask;
+            }
+            reached += 1;
+            edges += deg;
+        }
+        enqueue_binned<true>(P, first, r, deg, mask, 0, 0);
+    }
+    reached = warp_incl_scan(reached);
+    edges = warp_incl_scan(edges);
+    if (lane == 31) {
+        P.stats->reached = reached;
+        P.stats->edges = edges;
+        P.stats->levels = 1;
+    }
+}
+
+// Phase B of a batched level: lanes that reached v for the first time get
+// distance level + 1 and make v part of the next frontier with those lanes.
+__device__ void sweep_batch(const TraversalParams& P, int level, long long tid,
+                            long long nthreads) {
+    const int nslot = (level + 1) % 3, nxt = (level + 1) & 1;
+    const unsigned lane = lane_id();
+    long long my_pairs = 0, my_edges = 0;
+    const long long nround = (P.n + 31) / 32 * 32;  // warp-uniform trip count
+    for (long long v = tid; v < nround; v += nthreads) {
+        uint64_t fresh = 0ull;
+        long long deg = 0;
+        if (v < P.n) {
+            const uint64_t nx = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_next) + v);
+            if (nx != 0ull) {
+                const uint64_t vis =
+                    __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_visited) + v);
+                fresh = nx & ~vis;
+                P.lane_next[v] = 0ull;
+                if (fresh != 0ull) {
+                    P.lane_visited[v] = vis | fresh;
+                    deg = __ldg(P.off + v + 1) - __ldg(P.off + v);
+                    const int pc = __popcll(fresh);
+                    my_pairs += pc;
+                    my_edges += deg * pc;
+                }
+            }
+        }
+        // distances: loop over the union of new lanes in this warp
+        unsigned long long any = fresh;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) any |= __shfl_xor_sync(FULL_MASK, any, d);
+        if (any != 0ull) {
+            const int32_t cv = (fresh != 0ull) ? (P.new2old ? __ldg(P.new2old + v) : (int32_t)v) : 0;
+            while (any != 0ull) {
+                const int li = __ffsll((long long)any) - 1;
+                any &= any - 1ull;
+                if ((fresh >> li) & 1ull) write_lane_dist(P, li, cv, level + 1);
+            }
+        }
+        enqueue_binned<true>(P, fresh != 0ull, (int32_t)(v < P.n ? v : 0), deg, fresh, nxt, nslot);
+    }
+    // per-warp totals
+    my_pairs = warp_incl_scan(my_pairs);
+    my_edges = warp_incl_scan(my_edges);
+    if (lane == 31 && my_pairs > 0) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl[nslot].new_lanes),
+                  (unsigned long long)my_pairs);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats->edges),
+                  (unsigned long long)my_edges);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats->reached),
+                  (unsigned long long)my_pairs);
+    }
+}
+
+__device__ void book_batch_level(const TraversalParams& P, int level) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    unsigned long long* z = reinterpret_cast<unsigned long long*>(P.ctl + (level + 2) % 3);
+    for (int i = 0; i < (int)(sizeof(LevelCtl) / 8); ++i) z[i] = 0ull;
+}
+
+__global__ void __launch_bounds__(kBlock)
+bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
+    const long long nthreads = (long long)gridDim.x * kBlock;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    init_batch(P, tid, nthreads);
+    if (grid_barrier(P)) {
+        seed_batch(P);
+        if (grid_barrier(P)) {
+            for (int level = 0;; ++level) {
+                const LevelShape S = read_level(P, level);
+                if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) break;
+                if (P.dist_int8 && level + 1 > 126) {
+                    if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(P, kDevDepth);
+                    break;
+                }
+                book_batch_level(P, level);
+                expand_level<true>(P, S, level);
+                if (!grid_barrier(P)) break;
+                sweep_batch(P, level, tid, nthreads);
+                if (!grid_barrier(P)) break;
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    if (__ldcg(reinterpret_cast<const unsigned long long*>(
+                            &P.ctl[(level + 1) % 3].new_lanes)) > 0ull)
+                        P.stats->levels = level + 2;
+                }
+            }
+        }
+    }
+    kernel_exit(P);
+}
+
+__global__ void __launch_bounds__(kBlock)
+bfs_batch_step(const __grid_constant__ TraversalParams P) {
+    const long long nthreads = (long long)gridDim.x * kBlock;
+    const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    if (P.phase == 0) {
+        init_batch(P, tid, nthreads);
+    } else if (P.phase == 1) {
+        seed_batch(P);
+    } else if (P.phase == 2) {
+        const LevelShape S = read_level(P, P.level);
+        if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) return;
+        book_batch_level(P, P.level);
+        expand_level<true>(P, S, P.level);
+    } else {
+        sweep_batch(P, P.level, tid, nthreads);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            // levels is finalised by the host from new_lanes in host-loop mode
+        }
+    }
+}
+
+// ------------------------------------------------------ upload helpers
+// CSR validation: flags[0] |= 1 for a column out of range, |= 2 for a
+// decreasing offset.
+__global__ void csr_check_kernel(const int64_t* off, const int32_t* col, long long n, long long nnz,
+                                 int* flags) {
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int bad = 0;
+    for (long long e = tid; e < nnz; e += nthreads) {
+        const int32_t c = col[e];
+        if (c < 0 || (long long)c >= n) bad |= 1;
+    }
+    for (long long v = tid; v < n; v += nthreads)
+        if (off[v + 1] < off[v]) bad |= 2;
+    if (bad) atomicOr(flags, bad);
+}
+
+// Degree histogram by bin: counts[b] vertices and edges[b] entries.
+__global__ void degree_bins_kernel(const int64_t* off, long long n, int t_small, int t_large,
+                                   unsigned long long* counts, unsigned long long* edges,
+                                   unsigned long long* maxdeg) {
+    __shared__ unsigned long long s_c[kBins], s_e[kBins], s_m;
+    if (threadIdx.x < kBins) { s_c[threadIdx.x] = 0; s_e[threadIdx.x] = 0; }
+    if (threadIdx.x == 0) s_m = 0;
+    __syncthreads();
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    unsigned long long c[kBins] = {0, 0, 0}, e[kBins] = {0, 0, 0}, m = 0;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += nthreads) {
+        const long long d = off[v + 1] - off[v];
+        if (d <= 0) continue;
+        const int b = d < t_small ? 0 : (d < t_large ? 1 : 2);
+        c[b] += 1;
+        e[b] += (unsigned long long)d;
+        m = d > (long long)m ? (unsigned long long)d : m;
+    }
+    for (int b = 0; b < kBins; ++b) {
+        atomicAdd(&s_c[b], c[b]);
+        atomicAdd(&s_e[b], e[b]);
+    }
+    atomicMax(&s_m, m);
+    __syncthreads();
+    if (threadIdx.x < kBins) {
+        atomicAdd(&counts[threadIdx.x], s_c[threadIdx.x]);
+        atomicAdd(&edges[threadIdx.x], s_e[threadIdx.x]);
+    }
+    if (threadIdx.x == 0) atomicMax(maxdeg, s_m);
+}
+
+// -------------------------------------------------------- host wrappers
+const void* plain_persistent_fn() { return (const void*)bfs_plain_persistent; }
+const void* plain_step_fn() { return (const void*)bfs_plain_step; }
+const void* batch_persistent_fn() { return (const void*)bfs_batch_persistent; }
+const void* batch_step_fn() { return (const void*)bfs_batch_step; }
+
+cudaError_t launch_csr_check(const int64_t* off, const int32_t* col, long long n, long long nnz,
+                             int* flags, int sms, cudaStream_t s) {
+    csr_check_kernel<<<sms * 4, 512, 0, s>>>(off, col, n, nnz, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_degree_bins(const int64_t* off, long long n, int t_small, int t_large,
+                               unsigned long long* counts, unsigned long long* edges,
+                               unsigned long long* maxdeg, int sms, cudaStream_t s) {
+    degree_bins_kernel<<<sms * 2, 512, 0, s>>>(off, n, t_small, t_large, counts, edges, maxdeg);
+    return cudaGetLastError();
+}
+
+}  // namespace bfs

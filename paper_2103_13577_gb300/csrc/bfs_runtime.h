@@ -1,0 +1,99 @@
+// bfs_runtime.h -- host-side runtime objects behind the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/bfs.h"
+#include "bfs_internal.h"
+
+namespace bfs {
+
+// Device-memory source of a context: the caller's arena (first-fit free
+// list, 256-byte granules, coalescing on free) or cudaMalloc.
+class DeviceAllocator {
+public:
+    DeviceAllocator(void* arena, size_t bytes);
+    ~DeviceAllocator();
+    void* alloc(size_t bytes);           // nullptr when exhausted
+    void release(void* p);
+    size_t used() const;
+    size_t capacity() const;
+
+private:
+    mutable std::mutex mu_;
+    char* base_;
+    size_t cap_;
+    size_t used_ = 0;
+    std::map<size_t, size_t> free_;      // offset -> size (arena mode)
+    std::map<void*, size_t> live_;       // pointer -> size
+};
+
+// Per-traversal buffers of one graph: everything one launch touches besides
+// the graph itself and the caller's outputs.  Sized once from the degree
+// histogram (the paper's tight bound: no allocation inside the level loop).
+struct Workspace {
+    bool batched = false;
+    size_t bytes = 0;
+    uint32_t* visited = nullptr;
+    BinQueue q[2][kBins];
+    char* control = nullptr;           // LevelCtl[3] | GridBarrier | DevStats
+    LevelCtl* ctl = nullptr;
+    GridBarrier* bar = nullptr;
+    DevStats* stats = nullptr;
+    uint64_t* lane_visited = nullptr;
+    uint64_t* lane_next = nullptr;
+    int32_t* roots = nullptr;          // [64]
+    int32_t* dist_scratch = nullptr;   // host-output staging (plain: n; batched: none)
+    int32_t* parent_scratch = nullptr;
+    void* batch_dist_scratch = nullptr;  // batched host-output staging, 64 * n int32
+    DeviceAllocator* mem = nullptr;    // where the buffers came from
+};
+
+}  // namespace bfs
+
+struct bfs_context {
+    int device = 0;
+    int sms = 0;
+    size_t l2_bytes = 0;
+    bfs::DeviceAllocator* mem = nullptr;
+};
+
+struct bfs_graph {
+    bfs_context* ctx = nullptr;
+    int64_t n = 0, nnz = 0, max_degree = 0;
+    int64_t* d_off = nullptr;
+    int32_t* d_col = nullptr;
+    int32_t* d_new2old = nullptr;     // device numbering -> caller numbering
+    int32_t* d_old2new = nullptr;     // caller numbering -> device numbering
+    bool relabelled = false;
+    int32_t t_small = 32, t_large = 2048, chunk_warp = 1024, chunk_cta = 8192;
+    uint64_t bin_count[bfs::kBins] = {0, 0, 0};
+    uint64_t bin_edges[bfs::kBins] = {0, 0, 0};
+    bfs::Workspace* ws_plain = nullptr;
+    bfs::Workspace* ws_batch = nullptr;
+    size_t graph_bytes = 0;
+    int32_t grid_plain = 0, grid_batch = 0;
+    int32_t debug_stall = 0;
+    long long timeout_ns = 2000000000ll;
+    int32_t use_match_any = 0;
+    std::mutex mu;
+};
+
+namespace bfs {
+// helpers shared by the C ABI translation units
+void set_error(const std::string& msg);
+bfs_status cuda_fail(cudaError_t e, const char* what);
+Workspace* make_workspace(bfs_graph* g, DeviceAllocator* m, bool batched, cudaStream_t s,
+                          bfs_status* st);
+void free_workspace(bfs_graph* g, Workspace* ws);
+size_t workspace_bytes(const bfs_graph* g, bool batched, int nlanes);
+bfs_status run_batch_on(bfs_graph* g, Workspace* ws, const int32_t* roots, int32_t k, void* dist,
+                        cudaStream_t stream, uint32_t flags, int32_t grid);
+bfs_status batch_finish(bfs_graph* g, Workspace* ws, cudaStream_t stream, bfs_run_stats* stats);
+}  // namespace bfs

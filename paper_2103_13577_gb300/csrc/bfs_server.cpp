@@ -1,0 +1,411 @@
+// bfs_server.cpp -- continuous-batching query server behind bfs_submit /
+// bfs_poll.
+//
+// One dispatcher thread owns every launch.  Queries wait in a FIFO per
+// graph.  Whenever a stream slot is free and the server's device arena
+// (its memory budget) can hold a launch's traversal buffers and distance
+// rows, the dispatcher takes up to 64 waiting queries of one graph (graphs
+// served round robin), runs them as one batched traversal on that slot's
+// stream, enqueues the copies of each lane's row into the caller's buffer,
+// and records an event.  Completed events release the memory, which admits
+// the next launch -- so queries that arrive while others are on the GPU
+// join the next launch on a free slot, and launches on different slots
+// overlap on the device (each launch's persistent grid is sized to a share
+// of the SMs so several can be resident together).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "bfs_runtime.h"
+
+namespace bfs {
+
+struct Query {
+    bfs_ticket ticket = 0;
+    int32_t graph_id = 0;
+    int32_t root = 0;
+    int32_t* dist_out = nullptr;
+    bfs_status status = BFS_PENDING;
+};
+
+struct Launch {
+    int slot = -1;
+    int32_t graph_id = 0;
+    Workspace* ws = nullptr;
+    void* d_dist = nullptr;
+    std::vector<std::shared_ptr<Query>> lanes;
+    cudaEvent_t done = nullptr;
+};
+
+struct SlotState {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t event = nullptr;
+    bool busy = false;
+};
+
+}  // namespace bfs
+
+using namespace bfs;
+
+struct bfs_server {
+    bfs_context* ctx = nullptr;
+    size_t budget = 0;
+    void* arena = nullptr;
+    DeviceAllocator* mem = nullptr;
+    std::vector<bfs_graph*> graphs;
+    std::vector<std::deque<std::shared_ptr<Query>>> pending;
+    std::unordered_map<bfs_ticket, std::shared_ptr<Query>> tickets;
+    std::vector<SlotState> slots;
+    std::vector<Launch> inflight;
+    std::mutex mu;
+    std::condition_variable cv_work;   // wakes the dispatcher
+    std::condition_variable cv_done;   // wakes waiters
+    std::thread dispatcher;
+    bool stop = false;
+    bfs_ticket next_ticket = 1;
+    size_t rr = 0;
+    bfs_server_stats stats{};
+    size_t inflight_bytes = 0;
+};
+
+namespace bfs {
+
+static size_t launch_bytes(const bfs_graph* g, int k) {
+    return workspace_bytes(g, true, k) + 256 * 32 + (size_t)k * g->n * 4 + 4096;
+}
+
+// Runs with s->mu held.  Returns true when something was launched.
+static bool try_launch(bfs_server* s) {
+    int free_slot = -1;
+    for (size_t i = 0; i < s->slots.size(); ++i)
+        if (!s->slots[i].busy) {
+            free_slot = (int)i;
+            break;
+        }
+    if (free_slot < 0) return false;
+    const size_t ng = s->graphs.size();
+    for (size_t t = 0; t < ng; ++t) {
+        const size_t gid = (s->rr + t) % ng;
+        auto& q = s->pending[gid];
+        if (q.empty()) continue;
+        bfs_graph* g = s->graphs[gid];
+        const int k = (int)std::min<size_t>(64, q.size());
+        SlotState& sl = s->slots[free_slot];
+        bfs_status st = BFS_OK;
+        cudaSetDevice(s->ctx->device);
+        Workspace* ws = make_workspace(g, s->mem, true, sl.stream, &st);
+        void* d_dist = ws ? s->mem->alloc((size_t)k * g->n * 4) : nullptr;
+        if (!ws || !d_dist) {
+            if (ws) free_workspace(g, ws);
+            continue;  // does not fit now; another graph might, or wait for completions
+        }
+        Launch L;
+        L.slot = free_slot;
+        L.graph_id = (int32_t)gid;
+        L.ws = ws;
+        L.d_dist = d_dist;
+        std::vector<int32_t> roots;
+        for (int i = 0; i < k; ++i) {
+            L.lanes.push_back(q.front());
+            roots.push_back(q.front()->root);
+            q.pop_front();
+        }
+        // a share of the persistent grid so that launches on other slots
+        // can be resident at the same time
+        const int32_t share =
+            std::max<int32_t>(s->ctx->sms, g->grid_batch / (int32_t)s->slots.size());
+        st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, 0, share);
+        if (st == BFS_OK) {
+            for (int i = 0; i < k; ++i) {
+                cudaError_t e = cudaMemcpyAsync(L.lanes[i]->dist_out,
+                                                static_cast<int32_t*>(d_dist) + (size_t)i * g->n,
+                                                (size_t)g->n * 4, cudaMemcpyDeviceToHost, sl.stream);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(e, "result copy");
+                    break;
+                }
+            }
+        }
+        if (st == BFS_OK) {
+            cudaError_t e = cudaEventRecord(sl.event, sl.stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "event record");
+        }
+        if (st != BFS_OK) {
+            cudaStreamSynchronize(sl.stream);
+            for (auto& qq : L.lanes) qq->status = st;
+            s->stats.failed += k;
+            free_workspace(g, ws);
+            s->mem->release(d_dist);
+            s->cv_done.notify_all();
+            return true;
+        }
+        L.done = sl.event;
+        sl.busy = true;
+        s->stats.launches += 1;
+        s->stats.lanes += k;
+        s->inflight_bytes = s->mem->used();
+        s->stats.max_inflight_bytes =
+            std::max<int64_t>(s->stats.max_inflight_bytes, (int64_t)s->inflight_bytes);
+        s->inflight.push_back(std::move(L));
+        s->rr = (gid + 1) % ng;
+        return true;
+    }
+    return false;
+}
+
+// Runs with s->mu held.  Retires finished launches; returns how many.
+static int reap(bfs_server* s, bool block) {
+    int n = 0;
+    for (size_t i = 0; i < s->inflight.size();) {
+        Launch& L = s->inflight[i];
+        cudaError_t e = block ? cudaEventSynchronize(L.done) : cudaEventQuery(L.done);
+        if (e == cudaErrorNotReady) {
+            ++i;
+            continue;
+        }
+        bfs_status st = BFS_OK;
+        if (e != cudaSuccess) st = cuda_fail(e, "batched traversal");
+        if (st == BFS_OK) st = batch_finish(s->graphs[L.graph_id], L.ws, s->slots[L.slot].stream, nullptr);
+        for (auto& q : L.lanes) q->status = st;
+        if (st == BFS_OK) s->stats.completed += (int64_t)L.lanes.size();
+        else s->stats.failed += (int64_t)L.lanes.size();
+        free_workspace(s->graphs[L.graph_id], L.ws);
+        s->mem->release(L.d_dist);
+        s->slots[L.slot].busy = false;
+        s->inflight.erase(s->inflight.begin() + (long)i);
+        ++n;
+    }
+    if (n) s->cv_done.notify_all();
+    return n;
+}
+
+static void dispatcher_main(bfs_server* s) {
+    cudaSetDevice(s->ctx->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    for (;;) {
+        bool progressed = reap(s, false) > 0;
+        while (!s->stop && try_launch(s)) progressed = true;
+        bool waiting = false;
+        for (auto& q : s->pending)
+            if (!q.empty()) waiting = true;
+        if (s->stop && s->inflight.empty()) break;
+        if (!s->inflight.empty()) {
+            // poll completions without holding the lock for long
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(progressed ? 0 : 20));
+            lk.lock();
+        } else if (!waiting) {
+            s->cv_work.wait(lk, [&] {
+                if (s->stop) return true;
+                for (auto& q : s->pending)
+                    if (!q.empty()) return true;
+                return false;
+            });
+        } else if (!progressed) {
+            // queries wait but nothing fits and nothing is in flight: they can never run
+            for (size_t gid = 0; gid < s->pending.size(); ++gid) {
+                for (auto& q : s->pending[gid]) {
+                    q->status = BFS_ERR_BUDGET;
+                    s->stats.failed += 1;
+                }
+                s->pending[gid].clear();
+            }
+            s->cv_done.notify_all();
+        }
+    }
+}
+
+}  // namespace bfs
+
+extern "C" {
+
+bfs_status bfs_server_create(bfs_context* ctx, size_t memory_budget, int32_t num_streams,
+                             bfs_server** out) {
+    if (!ctx || !out) {
+        set_error("null argument");
+        return BFS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (num_streams < 1 || num_streams > 16 || memory_budget < (1u << 20)) {
+        set_error("num_streams must be 1..16 and the budget at least 1 MiB");
+        return BFS_ERR_INVALID_ARG;
+    }
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    bfs_server* s = new bfs_server();
+    s->ctx = ctx;
+    s->budget = memory_budget;
+    s->arena = ctx->mem->alloc(memory_budget);
+    if (!s->arena) {
+        delete s;
+        set_error("cannot reserve the server's memory budget on the device");
+        return BFS_ERR_NO_MEMORY;
+    }
+    s->mem = new DeviceAllocator(s->arena, memory_budget);
+    s->slots.resize((size_t)num_streams);
+    for (auto& sl : s->slots) {
+        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.event, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            bfs_status st = cuda_fail(e, "stream creation");
+            for (auto& x : s->slots) {
+                if (x.stream) cudaStreamDestroy(x.stream);
+                if (x.event) cudaEventDestroy(x.event);
+            }
+            delete s->mem;
+            ctx->mem->release(s->arena);
+            delete s;
+            return st;
+        }
+    }
+    s->dispatcher = std::thread(dispatcher_main, s);
+    *out = s;
+    return BFS_OK;
+}
+
+bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id) {
+    if (!s || !g || !graph_id) {
+        set_error("null argument");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->graphs.push_back(g);
+    s->pending.emplace_back();
+    *graph_id = (int32_t)s->graphs.size() - 1;
+    return BFS_OK;
+}
+
+bfs_status bfs_submit(bfs_server* s, int32_t graph_id, int32_t root, int32_t* dist_out,
+                      bfs_ticket* ticket) {
+    if (!s || !dist_out || !ticket) {
+        set_error("null argument");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (graph_id < 0 || (size_t)graph_id >= s->graphs.size()) {
+        set_error("unknown graph id");
+        return BFS_ERR_NOT_FOUND;
+    }
+    bfs_graph* g = s->graphs[(size_t)graph_id];
+    if (root < 0 || root >= g->n) {
+        set_error("root out of range");
+        return BFS_ERR_ROOT_RANGE;
+    }
+    if (s->stop) {
+        set_error("server is shutting down");
+        return BFS_ERR_CANCELLED;
+    }
+    if (launch_bytes(g, 1) > s->budget) {
+        set_error("one query on this graph needs more device memory than the budget");
+        return BFS_ERR_BUDGET;
+    }
+    auto q = std::make_shared<Query>();
+    q->ticket = s->next_ticket++;
+    q->graph_id = graph_id;
+    q->root = root;
+    q->dist_out = dist_out;
+    s->tickets[q->ticket] = q;
+    s->pending[(size_t)graph_id].push_back(q);
+    s->stats.submitted += 1;
+    *ticket = q->ticket;
+    s->cv_work.notify_one();
+    return BFS_OK;
+}
+
+bfs_status bfs_poll(bfs_server* s, bfs_ticket ticket) {
+    if (!s) {
+        set_error("null server");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) {
+        set_error("unknown ticket");
+        return BFS_ERR_NOT_FOUND;
+    }
+    return it->second->status;
+}
+
+bfs_status bfs_wait(bfs_server* s, bfs_ticket ticket, int64_t timeout_us) {
+    if (!s) {
+        set_error("null server");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) {
+        set_error("unknown ticket");
+        return BFS_ERR_NOT_FOUND;
+    }
+    std::shared_ptr<Query> q = it->second;
+    auto ready = [&] { return q->status != BFS_PENDING; };
+    if (timeout_us < 0) s->cv_done.wait(lk, ready);
+    else s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
+    return q->status;
+}
+
+bfs_status bfs_release(bfs_server* s, bfs_ticket ticket) {
+    if (!s) {
+        set_error("null server");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) {
+        set_error("unknown ticket");
+        return BFS_ERR_NOT_FOUND;
+    }
+    if (it->second->status == BFS_PENDING) {
+        set_error("ticket still pending");
+        return BFS_PENDING;
+    }
+    s->tickets.erase(it);
+    return BFS_OK;
+}
+
+bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out) {
+    if (!s || !out) {
+        set_error("null argument");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    *out = s->stats;
+    return BFS_OK;
+}
+
+bfs_status bfs_server_destroy(bfs_server* s) {
+    if (!s) {
+        set_error("null server");
+        return BFS_ERR_INVALID_ARG;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        for (auto& q : s->pending) {
+            for (auto& x : q) x->status = BFS_ERR_CANCELLED;
+            q.clear();
+        }
+        s->cv_work.notify_all();
+        s->cv_done.notify_all();
+    }
+    if (s->dispatcher.joinable()) s->dispatcher.join();
+    cudaSetDevice(s->ctx->device);
+    for (auto& sl : s->slots) {
+        cudaStreamSynchronize(sl.stream);
+        cudaStreamDestroy(sl.stream);
+        cudaEventDestroy(sl.event);
+    }
+    delete s->mem;
+    s->ctx->mem->release(s->arena);
+    delete s;
+    return BFS_OK;
+}
+
+}  // extern "C"

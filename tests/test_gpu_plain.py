@@ -1,0 +1,212 @@
+"""GPU parity of the single-source traversal against the CPU oracle.
+
+Distances must match bit-exactly; parents are accepted when they satisfy
+the Graph500-style invariants (several parents are valid).  Every case
+goes through the C ABI.  Bin thresholds and chunk sizes are varied so
+that each expansion path (warp gather, warp per vertex, CTA chunks, heavy
+vertices split over many CTAs) carries whole traversals on its own.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+from tests import graphs as G
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2103_13577_gb300 as bfs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = bfs.Context(0)
+    yield c
+    c.close()
+
+
+def run_gpu(g, n, root, flags=0, host=False):
+    if host:
+        dist = np.empty(n, dtype=np.int32)
+        parent = np.empty(n, dtype=np.int32)
+        g.run(root, dist, parent, flags=flags)
+        return dist, parent, g.sync()
+    dist = torch.empty(n, dtype=torch.int32, device="cuda")
+    parent = torch.empty(n, dtype=torch.int32, device="cuda")
+    g.run(root, dist, parent, flags=flags)
+    st = g.sync()
+    return dist.cpu().numpy(), parent.cpu().numpy(), st
+
+
+def assert_parity(off, col, root, dist, parent, stats, undirected=True):
+    d_ref, _, info = oracle.bfs(off, col, root)
+    assert np.array_equal(dist, d_ref), f"root {root}: {np.count_nonzero(dist != d_ref)} distances differ"
+    assert oracle.check_tree(off, col, root, dist, parent, undirected=undirected) == []
+    assert stats["status"] == 0
+    assert stats["reached"] == info["reached"]
+    assert stats["edges_scanned"] == info["edges_scanned"]
+    assert stats["levels"] == info["levels"]
+
+
+SMALL = [
+    ("path", G.path(300), [0, 150, 299]),
+    ("cycle", G.cycle(257), [0, 100]),
+    ("star", G.star(5000), [0, 17]),
+    ("grid", G.grid(40, 70), [0, 1234]),
+    ("tree", G.binary_tree(4095), [0, 2047]),
+    ("union", G.disjoint_union(G.path(50), G.star(300)), [3, 60]),
+    ("complete", G.complete(200), [5]),
+    ("isolated_root", G.disjoint_union((np.zeros(2, dtype=np.int64), np.zeros(0, dtype=np.int32)),
+                                       G.cycle(10)), [0]),
+]
+
+
+@pytest.mark.parametrize("name,graph,roots", SMALL, ids=[s[0] for s in SMALL])
+def test_closed_form_graphs(ctx, name, graph, roots):
+    off, col = graph
+    g = bfs.Graph(ctx, off, col)
+    for r in roots:
+        dist, parent, st = run_gpu(g, len(off) - 1, r)
+        assert_parity(off, col, r, dist, parent, st)
+    g.close()
+
+
+def test_single_vertex_graph(ctx):
+    off = np.zeros(2, dtype=np.int64)
+    col = np.zeros(0, dtype=np.int32)
+    g = bfs.Graph(ctx, off, col)
+    dist, parent, st = run_gpu(g, 1, 0)
+    assert dist.tolist() == [0] and parent.tolist() == [0]
+    assert st["levels"] == 1 and st["reached"] == 1 and st["edges_scanned"] == 0
+    g.close()
+
+
+def test_directed_graph(ctx):
+    off, col = G.random_graph(3000, 9000, 5, undirected=False)
+    g = bfs.Graph(ctx, off, col)
+    for r in (0, 7, 2999):
+        dist, parent, st = run_gpu(g, 3000, r)
+        assert_parity(off, col, r, dist, parent, st, undirected=False)
+    g.close()
+
+
+@pytest.fixture(scope="module")
+def kron16():
+    off, col = graphgen.kronecker(16, 8, seed=1)
+    return off, col, graphgen.pick_roots(off, 16, seed=2)
+
+
+BIN_SETTINGS = [
+    ("default", None),
+    ("all_small", (1 << 20, (1 << 20) + 1, 1024, 8192)),
+    ("all_warp", (1, 1 << 20, 128, 8192)),
+    ("all_cta", (1, 2, 1024, 1024)),
+    ("tiny_chunks", (8, 64, 128, 1024)),
+    ("wide_chunks", (64, 8192, 4096, 32768)),
+]
+
+
+@pytest.mark.parametrize("name,bins", BIN_SETTINGS, ids=[b[0] for b in BIN_SETTINGS])
+def test_kron16_all_roots_bins(ctx, kron16, name, bins):
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col)
+    if bins:
+        g.set_bins(*bins)
+    for r in roots:
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+    g.close()
+
+
+def test_kron16_host_loop_and_host_outputs(ctx, kron16):
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col)
+    for r in roots[:6]:
+        d1, p1, s1 = run_gpu(g, len(off) - 1, int(r), flags=bfs.BFS_HOST_LOOP)
+        assert_parity(off, col, int(r), d1, p1, s1)
+        d2, p2, s2 = run_gpu(g, len(off) - 1, int(r), host=True)
+        assert_parity(off, col, int(r), d2, p2, s2)
+    g.close()
+
+
+def test_match_any_visited_update(ctx, kron16):
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col)
+    g.set_option(bfs.BFS_OPT_WARP_AGGREGATE, 1)
+    for r in roots:
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+    g.close()
+
+
+def test_er_graph(ctx):
+    off, col = graphgen.erdos_renyi(15, 32, seed=3)
+    g = bfs.Graph(ctx, off, col)
+    for r in graphgen.pick_roots(off, 6, seed=4):
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+    g.close()
+
+
+def test_device_pointer_upload_and_arena(kron16):
+    off, col, roots = kron16
+    arena = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    c = bfs.Context(0, arena=arena)
+    g = bfs.Graph(c, torch.from_numpy(off).cuda(), torch.from_numpy(col).cuda())
+    used, cap = c.memory()
+    assert 0 < used <= cap == 256 << 20
+    for r in roots[:3]:
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+    g.close()
+    assert c.memory()[0] == 0
+    c.close()
+
+
+def test_errors(ctx):
+    off, col = G.path(10)
+    g = bfs.Graph(ctx, off, col)
+    d = np.empty(10, dtype=np.int32)
+    with pytest.raises(bfs.BfsError) as e:
+        g.run(10, d)
+    assert e.value.status == bfs.BFS_ERR_ROOT_RANGE
+    with pytest.raises(bfs.BfsError) as e:
+        g.run(-1, d)
+    assert e.value.status == bfs.BFS_ERR_ROOT_RANGE
+    g.close()
+    bad = col.copy()
+    bad[3] = 10
+    with pytest.raises(bfs.BfsError) as e:
+        bfs.Graph(ctx, off, bad)
+    assert e.value.status == bfs.BFS_ERR_INVALID_GRAPH
+    off2 = off.copy()
+    off2[5], off2[6] = off2[6], off2[5]
+    with pytest.raises(bfs.BfsError) as e:
+        bfs.Graph(ctx, off2, col)
+    assert e.value.status == bfs.BFS_ERR_INVALID_GRAPH
+    off3 = off.copy()
+    off3[-1] += 1
+    with pytest.raises(bfs.BfsError) as e:
+        bfs.Graph(ctx, off3, col)
+    assert e.value.status == bfs.BFS_ERR_INVALID_GRAPH
+
+
+def test_stream_ordering_on_torch_stream(ctx, kron16):
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col)
+    s = torch.cuda.Stream()
+    n = len(off) - 1
+    outs = []
+    with torch.cuda.stream(s):
+        for r in roots[:4]:
+            d = torch.empty(n, dtype=torch.int32, device="cuda")
+            g.run(int(r), d, None, stream=s)
+            outs.append(d.clone())
+    s.synchronize()
+    for r, d in zip(roots[:4], outs):
+        d_ref, _, _ = oracle.bfs(off, col, int(r))
+        assert np.array_equal(d.cpu().numpy(), d_ref)
+    g.close()

@@ -1,0 +1,83 @@
+"""Serving: queries on several resident graphs, submitted while others are
+on the device, packed into batched launches.  Each result equals the
+oracle (and hence the same query run alone), bit-exactly."""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import pytest
+
+import graphgen
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2103_13577_gb300 as bfs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def setup():
+    ctx = bfs.Context(0)
+    graphs = []
+    for scale, seed in ((12, 1), (13, 2), (14, 3)):
+        off, col = graphgen.kronecker(scale, 16, seed=seed)
+        graphs.append((off, col, bfs.Graph(ctx, off, col)))
+    yield ctx, graphs
+    for _, _, g in graphs:
+        g.close()
+    ctx.close()
+
+
+def test_mixed_queries_match_alone(setup):
+    ctx, graphs = setup
+    srv = bfs.Server(ctx, 512 << 20, num_streams=3)
+    gids = [srv.add_graph(g) for _, _, g in graphs]
+    rng = np.random.default_rng(0)
+    queries = []
+    for i in range(150):
+        gi = int(rng.integers(0, len(graphs)))
+        off, col, _ = graphs[gi]
+        root = int(graphgen.pick_roots(off, 1, seed=1000 + i)[0])
+        out = np.full(len(off) - 1, -7, dtype=np.int32)
+        t = srv.submit(gids[gi], root, out)
+        queries.append((gi, root, out, t))
+        if i % 10 == 0:
+            time.sleep(0.001)  # let some launches start while more arrive
+    for gi, root, out, t in queries:
+        assert srv.wait(t, 30_000_000) == bfs.BFS_OK
+        off, col, _ = graphs[gi]
+        ref, _, _ = oracle.bfs(off, col, root)
+        assert np.array_equal(out, ref)
+        srv.release(t)
+    st = srv.stats()
+    assert st["completed"] == 150 and st["failed"] == 0
+    assert st["launches"] < 150, "queries on the same graph were never packed together"
+    srv.close()
+
+
+def test_budget_rejection_and_poll(setup):
+    ctx, graphs = setup
+    srv = bfs.Server(ctx, 1 << 20, num_streams=1)
+    gid = srv.add_graph(graphs[2][2])
+    out = np.empty(len(graphs[2][0]) - 1, dtype=np.int32)
+    with pytest.raises(bfs.BfsError) as e:
+        srv.submit(gid, 0, out)
+    assert e.value.status == bfs.BFS_ERR_BUDGET
+    srv.close()
+    srv = bfs.Server(ctx, 256 << 20, num_streams=1)
+    gid = srv.add_graph(graphs[0][2])
+    off, col, _ = graphs[0]
+    out = np.empty(len(off) - 1, dtype=np.int32)
+    t = srv.submit(gid, 5, out)
+    deadline = time.time() + 30
+    while srv.poll(t) == bfs.BFS_PENDING and time.time() < deadline:
+        time.sleep(0.0005)
+    assert srv.poll(t) == bfs.BFS_OK
+    ref, _, _ = oracle.bfs(off, col, 5)
+    assert np.array_equal(out, ref)
+    with pytest.raises(bfs.BfsError) as e:
+        srv.poll(12345)
+    assert e.value.status == bfs.BFS_ERR_NOT_FOUND
+    srv.close()
