@@ -121,9 +121,12 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *                            issue one atomicOr (default 0).
  *   BFS_OPT_TIMEOUT_NS       limit of every device-side grid-barrier wait,
  *                            in ns (default 2e9); expiry ends the traversal
- *                            with BFS_ERR_TIMEOUT. */
+ *                            with BFS_ERR_TIMEOUT.
+ *   BFS_OPT_CTAS_PER_SM      2 or 3: resident CTAs per SM of the traversal
+ *                            kernels (register cap 128 or 80; default 2). */
 #define BFS_OPT_WARP_AGGREGATE  1
 #define BFS_OPT_TIMEOUT_NS      2
+#define BFS_OPT_CTAS_PER_SM     3
 bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value);
 
 /* ---- single-source traversal ----------------------------------------------

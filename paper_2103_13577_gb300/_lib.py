@@ -31,6 +31,7 @@ BFS_DIST_INT8 = 0x2
 BFS_HOST_LOOP = 0x4
 BFS_OPT_WARP_AGGREGATE = 1
 BFS_OPT_TIMEOUT_NS = 2
+BFS_OPT_CTAS_PER_SM = 3
 
 
 class BfsError(RuntimeError):

@@ -14,10 +14,10 @@
 namespace bfs {
 
 // kernels and launch helpers (bfs_kernels.cu)
-const void* plain_persistent_fn();
-const void* plain_step_fn();
-const void* batch_persistent_fn();
-const void* batch_step_fn();
+const void* plain_persistent_fn(int mb);
+const void* plain_step_fn(int mb);
+const void* batch_persistent_fn(int mb);
+const void* batch_step_fn(int mb);
 cudaError_t launch_csr_check(const int64_t* off, const int32_t* col, long long n, long long nnz,
                              int* flags, int sms, cudaStream_t s);
 cudaError_t launch_degree_bins(const int64_t* off, long long n, int t_small, int t_large,
@@ -295,22 +295,22 @@ static bfs_status run_plain(bfs_graph* g, Workspace* ws, int32_t root, int32_t* 
     P.dist = dist;
     P.parent = parent;
     P.root_caller = root;
-    if (!(flags & BFS_HOST_LOOP)) return launch_coop(plain_persistent_fn(), g->grid_plain, P, s);
+    if (!(flags & BFS_HOST_LOOP)) return launch_coop(plain_persistent_fn(g->min_blocks), g->grid_plain, P, s);
     // host-driven level loop: init, seed, then one launch per level
     bfs_status st;
     P.phase = 0;
-    if ((st = launch_plain_kernel(plain_step_fn(), g->grid_plain, P, s)) != BFS_OK) return st;
+    if ((st = launch_plain_kernel(plain_step_fn(g->min_blocks), g->grid_plain, P, s)) != BFS_OK) return st;
     P.phase = 1;
-    if ((st = launch_plain_kernel(plain_step_fn(), 1, P, s)) != BFS_OK) return st;
+    if ((st = launch_plain_kernel(plain_step_fn(g->min_blocks), 1, P, s)) != BFS_OK) return st;
     P.phase = 2;
     for (int level = 0;; ++level) {
         P.level = level;
-        if ((st = launch_plain_kernel(plain_step_fn(), g->grid_plain, P, s)) != BFS_OK) return st;
+        if ((st = launch_plain_kernel(plain_step_fn(g->min_blocks), g->grid_plain, P, s)) != BFS_OK) return st;
         LevelCtl c;
         if ((st = read_ctl(ws, (level + 1) % 3, &c, s)) != BFS_OK) return st;
         if (ctl_empty(c)) {
             P.level = level + 1;  // books the last level's discoveries
-            return launch_plain_kernel(plain_step_fn(), 1, P, s);
+            return launch_plain_kernel(plain_step_fn(g->min_blocks), 1, P, s);
         }
     }
 }
@@ -324,12 +324,12 @@ bfs_status run_batch_on(bfs_graph* g, Workspace* ws, const int32_t* roots, int32
     P.dist_int8 = (flags & BFS_DIST_INT8) ? 1 : 0;
     for (int i = 0; i < k; ++i) P.roots[i] = roots[i];
     P.dist = static_cast<int32_t*>(dist);
-    if (!(flags & BFS_HOST_LOOP)) return launch_coop(batch_persistent_fn(), grid, P, s);
+    if (!(flags & BFS_HOST_LOOP)) return launch_coop(batch_persistent_fn(g->min_blocks), grid, P, s);
     bfs_status st;
     P.phase = 0;
-    if ((st = launch_plain_kernel(batch_step_fn(), grid, P, s)) != BFS_OK) return st;
+    if ((st = launch_plain_kernel(batch_step_fn(g->min_blocks), grid, P, s)) != BFS_OK) return st;
     P.phase = 1;
-    if ((st = launch_plain_kernel(batch_step_fn(), 1, P, s)) != BFS_OK) return st;
+    if ((st = launch_plain_kernel(batch_step_fn(g->min_blocks), 1, P, s)) != BFS_OK) return st;
     for (int level = 0;; ++level) {
         LevelCtl c;
         if ((st = read_ctl(ws, level % 3, &c, s)) != BFS_OK) return st;
@@ -338,9 +338,9 @@ bfs_status run_batch_on(bfs_graph* g, Workspace* ws, const int32_t* roots, int32
             return fail(BFS_ERR_DEPTH_OVERFLOW, "int8 distances: level above 126");
         P.level = level;
         P.phase = 2;
-        if ((st = launch_plain_kernel(batch_step_fn(), grid, P, s)) != BFS_OK) return st;
+        if ((st = launch_plain_kernel(batch_step_fn(g->min_blocks), grid, P, s)) != BFS_OK) return st;
         P.phase = 3;
-        if ((st = launch_plain_kernel(batch_step_fn(), grid, P, s)) != BFS_OK) return st;
+        if ((st = launch_plain_kernel(batch_step_fn(g->min_blocks), grid, P, s)) != BFS_OK) return st;
         LevelCtl nc;
         if ((st = read_ctl(ws, (level + 1) % 3, &nc, s)) != BFS_OK) return st;
         if (nc.new_lanes > 0) {
@@ -535,8 +535,8 @@ bfs_status bfs_graph_upload(bfs_context* ctx, const int64_t* row_off, const int3
     }
     bfs_status st = compute_bins(g, s);
     if (st != BFS_OK) return cleanup(st);
-    if ((st = grid_size(g, plain_persistent_fn(), &g->grid_plain)) != BFS_OK) return cleanup(st);
-    if ((st = grid_size(g, batch_persistent_fn(), &g->grid_batch)) != BFS_OK) return cleanup(st);
+    if ((st = grid_size(g, plain_persistent_fn(g->min_blocks), &g->grid_plain)) != BFS_OK) return cleanup(st);
+    if ((st = grid_size(g, batch_persistent_fn(g->min_blocks), &g->grid_batch)) != BFS_OK) return cleanup(st);
     Workspace* ws = nullptr;
     if ((st = ensure_workspace(g, false, s, &ws)) != BFS_OK) return cleanup(st);
     e = cudaStreamSynchronize(s);
@@ -695,6 +695,13 @@ bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value) {
         if (value <= 0) return fail(BFS_ERR_INVALID_ARG, "timeout must be positive");
         g->timeout_ns = value;
         return BFS_OK;
+    case BFS_OPT_CTAS_PER_SM: {
+        if (value != 2 && value != 3) return fail(BFS_ERR_INVALID_ARG, "value must be 2 or 3");
+        g->min_blocks = (int32_t)value;
+        bfs_status st = grid_size(g, plain_persistent_fn(g->min_blocks), &g->grid_plain);
+        if (st == BFS_OK) st = grid_size(g, batch_persistent_fn(g->min_blocks), &g->grid_batch);
+        return st;
+    }
     default: return fail(BFS_ERR_INVALID_ARG, "unknown option");
     }
 }

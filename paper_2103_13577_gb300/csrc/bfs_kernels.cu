@@ -133,14 +133,73 @@ __device__ void kernel_exit(const TraversalParams& P) {
 }
 
 // --------------------------------------------------------------- enqueue
-// Warp-collective: every lane calls it; lanes with ok append (u, deg, mask)
-// to the degree bin of deg in the next frontier.  One 64-bit atomicAdd per
-// bin and warp reserves both the queue slots and the edge range.
+// Discovered vertices are staged per warp in shared memory and appended to
+// the next frontier 64 at a time: one 64-bit atomicAdd per bin reserves
+// both the queue slots and the edge range of the whole group (the bin
+// counter packs entries << 34 | edge prefix), so the hot counters see one
+// atomic per 64 discoveries instead of one per warp step.
+constexpr int kStageCap = 64;
+
 template <bool kBatch>
-__device__ __forceinline__ void enqueue_binned(const TraversalParams& P, bool ok, int32_t u,
-                                               long long deg, uint64_t mask, int nxt,
-                                               int nslot) {
-    ok = ok && deg > 0;  // nothing to expand from a vertex without out-edges
+struct Stage {
+    int32_t v[kBins][kStageCap];
+    int32_t deg[kBins][kStageCap];
+    unsigned long long mask[kBatch ? kBins : 1][kBatch ? kStageCap : 1];
+    int cnt[kBins];
+};
+
+// Warp-collective: appends the staged entries of bin b to the next frontier.
+template <bool kBatch>
+__device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>& S, int b,
+                                         int nxt, int nslot) {
+    const unsigned lane = lane_id();
+    const int n = S.cnt[b];
+    if (n == 0) return;
+    const int i0 = (int)lane, i1 = (int)lane + 32;
+    const long long d0 = i0 < n ? S.deg[b][i0] : 0, d1 = i1 < n ? S.deg[b][i1] : 0;
+    const long long incl0 = warp_incl_scan(d0);
+    const long long tot0 = __shfl_sync(FULL_MASK, incl0, 31);
+    const long long incl1 = warp_incl_scan(d1) + tot0;
+    const long long tot = __shfl_sync(FULL_MASK, incl1, 31);
+    unsigned long long basep = 0ull;
+    if (lane == 0)
+        basep = atomicAdd(&P.ctl[nslot].packed[b],
+                          ((unsigned long long)n << kCountShift) + (unsigned long long)tot);
+    basep = __shfl_sync(FULL_MASK, basep, 0);
+    const BinQueue& Q = P.q[nxt][b];
+    const long long C = (b == 1) ? P.chunk_warp : P.chunk_cta;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = h ? i1 : i0;
+        if (i >= n) continue;
+        const long long d = h ? d1 : d0;
+        const long long pos = (long long)(basep >> kCountShift) + i;
+        const long long eo = (long long)(basep & kEdgeMask) + (h ? incl1 : incl0) - d;
+        if (pos >= Q.cap) {
+            raise_status(P, kDevOverflow);
+            continue;
+        }
+        Q.v[pos] = S.v[b][i];
+        if (kBatch) Q.mask[pos] = S.mask[kBatch ? b : 0][kBatch ? i : 0];
+        if (b > 0) {
+            Q.eoff[pos] = eo;
+            for (long long c = (eo + C - 1) / C; c * C < eo + d; ++c) {
+                if (c < Q.chunk_cap) Q.chunk[c] = (int32_t)pos;
+                else raise_status(P, kDevOverflow);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) S.cnt[b] = 0;
+    __syncwarp();
+}
+
+// Warp-collective: lanes with ok stage (u, deg, mask) into the bin of deg.
+// Vertices without out-edges are never queued (nothing to expand).
+template <bool kBatch>
+__device__ __forceinline__ void stage_push(const TraversalParams& P, Stage<kBatch>& S, bool ok,
+                                           int32_t u, int deg, uint64_t mask, int nxt, int nslot) {
+    ok = ok && deg > 0;
     const int bin = deg < P.t_small ? 0 : (deg < P.t_large ? 1 : 2);
     const unsigned lane = lane_id();
 #pragma unroll
@@ -148,130 +207,192 @@ __device__ __forceinline__ void enqueue_binned(const TraversalParams& P, bool ok
         const bool mine = ok && bin == b;
         const unsigned m = __ballot_sync(FULL_MASK, mine);
         if (m == 0u) continue;
-        const long long d = mine ? deg : 0ll;
-        const long long incl = warp_incl_scan(d);
-        const long long tot = __shfl_sync(FULL_MASK, incl, 31);
-        unsigned long long basep = 0ull;
-        if (lane == 0)
-            basep = atomicAdd(&P.ctl[nslot].packed[b],
-                              ((unsigned long long)__popc(m) << kCountShift) +
-                                  (unsigned long long)tot);
-        basep = __shfl_sync(FULL_MASK, basep, 0);
+        int n0 = S.cnt[b];
+        const int k = __popc(m);
+        if (n0 + k > kStageCap) {
+            stage_flush<kBatch>(P, S, b, nxt, nslot);
+            n0 = 0;
+        }
         if (mine) {
-            const BinQueue& Q = P.q[nxt][b];
-            const long long pos = (long long)(basep >> kCountShift) + __popc(m & lanemask_lt());
-            const long long eo = (long long)(basep & kEdgeMask) + incl - d;
-            if (pos < Q.cap) {
-                Q.v[pos] = u;
-                if (kBatch) Q.mask[pos] = mask;
-                if (b > 0) {
-                    Q.eoff[pos] = eo;
-                    const long long C = (b == 1) ? P.chunk_warp : P.chunk_cta;
-                    for (long long c = (eo + C - 1) / C; c * C < eo + d; ++c) {
-                        if (c < Q.chunk_cap) Q.chunk[c] = (int32_t)pos;
-                        else raise_status(P, kDevOverflow);
-                    }
-                }
-            } else {
-                raise_status(P, kDevOverflow);
-            }
+            const int i = n0 + __popc(m & lanemask_lt());
+            S.v[b][i] = u;
+            S.deg[b][i] = deg;
+            if (kBatch) S.mask[kBatch ? b : 0][kBatch ? i : 0] = mask;
         }
+        __syncwarp();
+        if (lane == 0) S.cnt[b] = n0 + k;
+        __syncwarp();
     }
-}
-
-// ----------------------------------------------------------------- visits
-// Plain traversal: claim u through the visited bitmap.  Warp-collective.
-__device__ __forceinline__ void visit_plain(const TraversalParams& P, bool valid, int32_t u,
-                                            int32_t v, int level, int nxt, int nslot) {
-    const unsigned lane = lane_id();
-    bool win = false;
-    uint32_t* wp = P.visited + (valid ? (u >> 5) : 0);
-    const uint32_t bit = 1u << (u & 31);
-    bool need = false;
-    if (valid) need = (*wp & bit) == 0u;  // may be stale: bits only go 0 -> 1
-    if (P.use_match_any) {
-        const unsigned needm = __ballot_sync(FULL_MASK, need);
-        if (need) {
-            const unsigned peers = __match_any_sync(needm, u >> 5);
-            const uint32_t bits = __reduce_or_sync(peers, bit);
-            const int leader = __ffs(peers) - 1;
-            uint32_t old = 0u;
-            if ((int)lane == leader) old = atomicOr(wp, bits);
-            old = __shfl_sync(peers, old, leader);
-            const unsigned same = __match_any_sync(peers, u);
-            win = ((old & bit) == 0u) && ((int)lane == __ffs(same) - 1);
-        }
-    } else if (need) {
-        win = (atomicOr(wp, bit) & bit) == 0u;
-    }
-    const unsigned winm = __ballot_sync(FULL_MASK, win);
-    if (winm == 0u) return;
-    long long deg = 0;
-    if (win) {
-        const int32_t cu = P.new2old ? __ldg(P.new2old + u) : u;
-        const int32_t cv = P.new2old ? __ldg(P.new2old + v) : v;
-        P.dist[cu] = level + 1;
-        if (P.parent) P.parent[cu] = cv;
-        const long long b0 = __ldg(P.off + u);
-        deg = __ldg(P.off + u + 1) - b0;
-    }
-    if (lane == 0) atomicAdd(&P.ctl[nslot].discovered, (unsigned)__popc(winm));
-    enqueue_binned<false>(P, win, u, deg, 0ull, nxt, nslot);
-}
-
-// Batched traversal, phase A: OR the entry's lanes that u has not seen into
-// next[u].  visited only changes in phase B, so a cached value is safe as a
-// filter.  Warp-collective (for symmetry with visit_plain; no warp ops).
-__device__ __forceinline__ void visit_batch(const TraversalParams& P, bool valid, int32_t u,
-                                            uint64_t mask) {
-    if (!valid) return;
-    const uint64_t m = mask & ~P.lane_visited[u];
-    if (m == 0ull) return;
-    unsigned long long* np = (unsigned long long*)(P.lane_next + u);
-    if ((m & ~*np) != 0ull) atomicOr(np, (unsigned long long)m);
 }
 
 template <bool kBatch>
-__device__ __forceinline__ void visit(const TraversalParams& P, bool valid, int32_t u, int32_t v,
-                                      uint64_t mask, int level, int nxt, int nslot) {
-    if (kBatch) visit_batch(P, valid, u, mask);
-    else visit_plain(P, valid, u, v, level, nxt, nslot);
+__device__ __forceinline__ void stage_flush_all(const TraversalParams& P, Stage<kBatch>& S,
+                                                int nxt, int nslot) {
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) stage_flush<kBatch>(P, S, b, nxt, nslot);
+}
+
+template <bool kBatch>
+__device__ __forceinline__ void stage_init(Stage<kBatch>& S) {
+    if (lane_id() < (unsigned)kBins) S.cnt[lane_id()] = 0;
+    __syncwarp();
+}
+
+// ----------------------------------------------------------------- visits
+// K edges per lane at once: all K visited-bitmap probes are issued before
+// any result is used, then the atomics, so a warp keeps K random accesses
+// in flight instead of one.
+template <int K>
+__device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<false>& S,
+                                              const bool (&ok)[K], const int32_t (&u)[K],
+                                              const int32_t (&v)[K], int level, int nxt,
+                                              int nslot, int& my_disc) {
+    uint32_t w[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = ok[j] ? P.visited[u[j] >> 5] : 0xffffffffu;
+    bool win[K];
+    bool any = false;
+    if (P.use_match_any) {
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint32_t bit = 1u << (u[j] & 31);
+            const bool need = (w[j] & bit) == 0u;
+            const unsigned needm = __ballot_sync(FULL_MASK, need);
+            win[j] = false;
+            if (need) {
+                const unsigned peers = __match_any_sync(needm, u[j] >> 5);
+                const uint32_t bits = __reduce_or_sync(peers, bit);
+                const int leader = __ffs(peers) - 1;
+                uint32_t old = 0u;
+                if ((int)lane_id() == leader) old = atomicOr(P.visited + (u[j] >> 5), bits);
+                old = __shfl_sync(peers, old, leader);
+                const unsigned same = __match_any_sync(peers, u[j]);
+                win[j] = ((old & bit) == 0u) && ((int)lane_id() == __ffs(same) - 1);
+            }
+            any |= win[j];
+        }
+    } else {
+        uint32_t old[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            const uint32_t bit = 1u << (u[j] & 31);
+            old[j] = bit;
+            if ((w[j] & bit) == 0u) old[j] = atomicOr(P.visited + (u[j] >> 5), bit);
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            win[j] = (old[j] & (1u << (u[j] & 31))) == 0u;
+            any |= win[j];
+        }
+    }
+    if (__ballot_sync(FULL_MASK, any) == 0u) return;
+    long long b0[K], b1[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        b0[j] = 0;
+        b1[j] = 0;
+        if (win[j]) {
+            b0[j] = __ldg(P.off + u[j]);
+            b1[j] = __ldg(P.off + u[j] + 1);
+            const int32_t cu = P.new2old ? __ldg(P.new2old + u[j]) : u[j];
+            const int32_t cv = P.new2old ? __ldg(P.new2old + v[j]) : v[j];
+            P.dist[cu] = level + 1;
+            if (P.parent) P.parent[cu] = cv;
+            ++my_disc;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (__ballot_sync(FULL_MASK, win[j]) == 0u) continue;
+        stage_push<false>(P, S, win[j], u[j], (int)(b1[j] - b0[j]), 0ull, nxt, nslot);
+    }
+}
+
+// Batched traversal, phase A: OR the lanes of the frontier entry that u has
+// not seen yet into next[u].  visited only changes in phase B, so a cached
+// value is a safe filter; next[u] is read first so that lanes already
+// present skip the atomic (a fire-and-forget red.or otherwise).
+template <int K>
+__device__ __forceinline__ void visit_batch_k(const TraversalParams& P, const bool (&ok)[K],
+                                              const int32_t (&u)[K],
+                                              const uint64_t (&mask)[K]) {
+    uint64_t m[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) m[j] = ok[j] ? (mask[j] & ~P.lane_visited[u[j]]) : 0ull;
+    uint64_t nx[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) nx[j] = m[j] ? P.lane_next[u[j]] : ~0ull;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+        if ((m[j] & ~nx[j]) != 0ull)
+            atomicOr(reinterpret_cast<unsigned long long*>(P.lane_next + u[j]),
+                     (unsigned long long)m[j]);
+}
+
+template <bool kBatch, int K>
+__device__ __forceinline__ void visit_k(const TraversalParams& P, Stage<kBatch>& S,
+                                        const bool (&ok)[K], const int32_t (&u)[K],
+                                        const int32_t (&v)[K], const uint64_t (&mask)[K],
+                                        int level, int nxt, int nslot, int& my_disc) {
+    if constexpr (kBatch) visit_batch_k<K>(P, ok, u, mask);
+    else visit_plain_k<K>(P, S, ok, u, v, level, nxt, nslot, my_disc);
 }
 
 // ------------------------------------------------------------ expansion
 // One column segment col[a, b) of vertex v, read by a group of warps with
 // 128-bit loads (start rounded down to 16 bytes; col is padded so the
-// rounded reads stay inside the allocation).  wbase/wstride give this
-// warp's first 256-entry block and the stride between its blocks.
+// rounded reads stay inside the allocation).  wbase/wstride place this
+// warp's 256-entry blocks; a segment that fits in 128 entries uses one
+// 128-bit load per lane.
 template <bool kBatch>
-__device__ __forceinline__ void expand_segment(const TraversalParams& P, long long a, long long b,
-                                               int32_t v, uint64_t mask, int level, int nxt,
-                                               int nslot, long long wbase, long long wstride) {
+__device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<kBatch>& S,
+                                               long long a, long long b, int32_t v, uint64_t mask,
+                                               int level, int nxt, int nslot, long long wbase,
+                                               long long wstride, int& my_disc) {
     const unsigned lane = lane_id();
     const long long a4 = a & ~3ll;
+    int32_t vv[8];
+    uint64_t mm[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        vv[j] = v;
+        mm[j] = mask;
+    }
+    if (wbase == 0 && wstride == 256 && b - a4 <= 128) {
+        const long long p0 = a4 + 4 * lane;
+        int4 x0 = make_int4(0, 0, 0, 0);
+        if (p0 < b) x0 = __ldcs(reinterpret_cast<const int4*>(P.col + p0));
+        const bool ok[4] = {p0 >= a && p0 < b, p0 + 1 >= a && p0 + 1 < b,
+                            p0 + 2 >= a && p0 + 2 < b, p0 + 3 >= a && p0 + 3 < b};
+        const int32_t u[4] = {x0.x, x0.y, x0.z, x0.w};
+        const int32_t v4[4] = {v, v, v, v};
+        const uint64_t m4[4] = {mask, mask, mask, mask};
+        visit_k<kBatch, 4>(P, S, ok, u, v4, m4, level, nxt, nslot, my_disc);
+        return;
+    }
     for (long long pw = a4 + wbase; pw < b; pw += wstride) {
         const long long p0 = pw + 4 * lane;
         const long long p1 = p0 + 128;
         int4 x0 = make_int4(0, 0, 0, 0), x1 = make_int4(0, 0, 0, 0);
         if (p0 < b) x0 = __ldcs(reinterpret_cast<const int4*>(P.col + p0));
         if (p1 < b) x1 = __ldcs(reinterpret_cast<const int4*>(P.col + p1));
-        visit<kBatch>(P, p0 >= a && p0 < b, x0.x, v, mask, level, nxt, nslot);
-        visit<kBatch>(P, p0 + 1 >= a && p0 + 1 < b, x0.y, v, mask, level, nxt, nslot);
-        visit<kBatch>(P, p0 + 2 >= a && p0 + 2 < b, x0.z, v, mask, level, nxt, nslot);
-        visit<kBatch>(P, p0 + 3 >= a && p0 + 3 < b, x0.w, v, mask, level, nxt, nslot);
-        visit<kBatch>(P, p1 >= a && p1 < b, x1.x, v, mask, level, nxt, nslot);
-        visit<kBatch>(P, p1 + 1 >= a && p1 + 1 < b, x1.y, v, mask, level, nxt, nslot);
-        visit<kBatch>(P, p1 + 2 >= a && p1 + 2 < b, x1.z, v, mask, level, nxt, nslot);
-        visit<kBatch>(P, p1 + 3 >= a && p1 + 3 < b, x1.w, v, mask, level, nxt, nslot);
+        const bool ok[8] = {p0 >= a && p0 < b,         p0 + 1 >= a && p0 + 1 < b,
+                            p0 + 2 >= a && p0 + 2 < b, p0 + 3 >= a && p0 + 3 < b,
+                            p1 >= a && p1 < b,         p1 + 1 >= a && p1 + 1 < b,
+                            p1 + 2 >= a && p1 + 2 < b, p1 + 3 >= a && p1 + 3 < b};
+        const int32_t u[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        visit_k<kBatch, 8>(P, S, ok, u, vv, mm, level, nxt, nslot, my_disc);
     }
 }
 
 // Bin 0: 32 frontier vertices per warp, one per lane; their edges are laid
-// end to end by an exclusive scan and consumed 64 per round, lane l taking
-// edges l and l+32 and finding its owner vertex by a shuffle binary search.
+// end to end by an exclusive scan and consumed 256 per round, lane l taking
+// edges l + 32 j (j < 8) and finding each edge's owner vertex by a
+// shuffle binary search over the scan.
 template <bool kBatch>
-__device__ void expand_small_group(const TraversalParams& P, int cur, long long grp,
-                                   long long cnt, int level, int nxt, int nslot) {
+__device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, int cur,
+                                   long long grp, long long cnt, int level, int nxt, int nslot,
+                                   int& my_disc) {
     const BinQueue& Q = P.q[cur][0];
     const unsigned lane = lane_id();
     const long long i = grp * 32 + lane;
@@ -288,41 +409,36 @@ __device__ void expand_small_group(const TraversalParams& P, int cur, long long 
     const int incl = warp_incl_scan(deg);
     const int excl = incl - deg;
     const int total = __shfl_sync(FULL_MASK, incl, 31);
-    for (int e0 = 0; e0 < total; e0 += 64) {
-        int ea = e0 + (int)lane, eb = ea + 32;
-        int oa = 0, ob = 0;
+    for (int e0 = 0; e0 < total; e0 += 256) {
+        bool ok[8];
+        int32_t u[8], vv[8];
+        uint64_t mm[8];
 #pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            const int ca = oa + s, cb = ob + s;
-            const int xa = __shfl_sync(FULL_MASK, excl, ca & 31);
-            const int xb = __shfl_sync(FULL_MASK, excl, cb & 31);
-            if (xa <= ea) oa = ca;
-            if (xb <= eb) ob = cb;
+        for (int j = 0; j < 8; ++j) {
+            const int e = e0 + 32 * j + (int)lane;
+            int o = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const int c = o + s;
+                if (__shfl_sync(FULL_MASK, excl, c & 31) <= e) o = c;
+            }
+            const long long bo = __shfl_sync(FULL_MASK, base, o);
+            const int xo = __shfl_sync(FULL_MASK, excl, o);
+            vv[j] = __shfl_sync(FULL_MASK, v, o);
+            mm[j] = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, o) : 0ull;
+            ok[j] = e < total;
+            u[j] = ok[j] ? __ldcs(P.col + bo + (e - xo)) : 0;
         }
-        const long long ba = __shfl_sync(FULL_MASK, base, oa);
-        const long long bb = __shfl_sync(FULL_MASK, base, ob);
-        const int xa = __shfl_sync(FULL_MASK, excl, oa);
-        const int xb = __shfl_sync(FULL_MASK, excl, ob);
-        const int32_t va = __shfl_sync(FULL_MASK, v, oa);
-        const int32_t vb = __shfl_sync(FULL_MASK, v, ob);
-        uint64_t ma = 0ull, mb = 0ull;
-        if (kBatch) {
-            ma = __shfl_sync(FULL_MASK, (unsigned long long)mask, oa);
-            mb = __shfl_sync(FULL_MASK, (unsigned long long)mask, ob);
-        }
-        const bool oka = ea < total, okb = eb < total;
-        const int32_t ua = oka ? __ldcs(P.col + ba + (ea - xa)) : 0;
-        const int32_t ub = okb ? __ldcs(P.col + bb + (eb - xb)) : 0;
-        visit<kBatch>(P, oka, ua, va, ma, level, nxt, nslot);
-        visit<kBatch>(P, okb, ub, vb, mb, level, nxt, nslot);
+        visit_k<kBatch, 8>(P, S, ok, u, vv, mm, level, nxt, nslot, my_disc);
     }
 }
 
 // Bin 1: one warp per chunk of chunk_warp edges; inside it, one vertex
 // segment at a time, the whole warp reading it with 128-bit loads.
 template <bool kBatch>
-__device__ void expand_warp_chunk(const TraversalParams& P, int cur, long long chunk,
-                                  long long cnt, long long E, int level, int nxt, int nslot) {
+__device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
+                                  long long chunk, long long cnt, long long E, int level, int nxt,
+                                  int nslot, int& my_disc) {
     const BinQueue& Q = P.q[cur][1];
     const unsigned lane = lane_id();
     const long long cs = chunk * (long long)P.chunk_warp;
@@ -350,8 +466,8 @@ __device__ void expand_warp_chunk(const TraversalParams& P, int cur, long long c
             const int32_t vk = __shfl_sync(FULL_MASK, v, k);
             const uint64_t mk = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, k) : 0ull;
             const long long lo = max(eok, cs), hi = min(eok + (ek - bk), ce);
-            expand_segment<kBatch>(P, bk + (lo - eok), bk + (hi - eok), vk, mk, level, nxt, nslot,
-                                   0, 256);
+            expand_segment<kBatch>(P, S, bk + (lo - eok), bk + (hi - eok), vk, mk, level, nxt,
+                                   nslot, 0, 256, my_disc);
         }
         if (nent < 32) break;
         i += 32;
@@ -361,11 +477,12 @@ __device__ void expand_warp_chunk(const TraversalParams& P, int cur, long long c
 // Bin 2: one CTA per chunk of chunk_cta edges (a heavy vertex spans many
 // chunks, hence many CTAs); the CTA's warps interleave over each segment.
 template <bool kBatch>
-__device__ void expand_cta_chunk(const TraversalParams& P, int cur, long long chunk,
-                                 long long cnt, long long E, int level, int nxt, int nslot) {
+__device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
+                                 long long chunk, long long cnt, long long E, int level, int nxt,
+                                 int nslot, int& my_disc) {
     __shared__ long long s_eo[kBlock], s_base[kBlock], s_end[kBlock];
     __shared__ int32_t s_v[kBlock];
-    __shared__ unsigned long long s_mask[kBlock];
+    __shared__ unsigned long long s_mask[kBatch ? kBlock : 1];
     const BinQueue& Q = P.q[cur][2];
     const int warp = threadIdx.x >> 5;
     const long long cs = chunk * (long long)P.chunk_cta;
@@ -382,15 +499,17 @@ __device__ void expand_cta_chunk(const TraversalParams& P, int cur, long long ch
             s_eo[threadIdx.x] = eo;
             s_base[threadIdx.x] = __ldg(P.off + v);
             s_end[threadIdx.x] = __ldg(P.off + v + 1);
-            s_mask[threadIdx.x] =
-                kBatch ? __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij) : 0ull;
+            if (kBatch)
+                s_mask[kBatch ? threadIdx.x : 0] =
+                    __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij);
         }
         const int nent = __syncthreads_count(ok);
         for (int k = 0; k < nent; ++k) {
             const long long eok = s_eo[k], bk = s_base[k];
             const long long lo = max(eok, cs), hi = min(eok + (s_end[k] - bk), ce);
-            expand_segment<kBatch>(P, bk + (lo - eok), bk + (hi - eok), s_v[k], s_mask[k], level,
-                                   nxt, nslot, (long long)warp * 256, 256ll * kWarps);
+            expand_segment<kBatch>(P, S, bk + (lo - eok), bk + (hi - eok), s_v[k],
+                                   kBatch ? s_mask[kBatch ? k : 0] : 0ull, level, nxt, nslot,
+                                   (long long)warp * 256, 256ll * kWarps, my_disc);
         }
         __syncthreads();
         if (nent < kBlock) break;
@@ -400,7 +519,7 @@ __device__ void expand_cta_chunk(const TraversalParams& P, int cur, long long ch
 
 struct LevelShape {
     long long cnt[kBins], edges[kBins];
-    long long n_cta, chunks_warp, n_warp_items, groups_small, n_small_items, total;
+    long long n_cta, chunks_warp, groups_small;
     unsigned discovered;
 };
 
@@ -420,38 +539,55 @@ __device__ __forceinline__ LevelShape read_level(const TraversalParams& P, int l
     s.n_cta = min((s.edges[2] + P.chunk_cta - 1) / P.chunk_cta, (long long)P.q[cur][2].chunk_cap);
     s.chunks_warp =
         min((s.edges[1] + P.chunk_warp - 1) / P.chunk_warp, (long long)P.q[cur][1].chunk_cap);
-    s.n_warp_items = (s.chunks_warp + kWarps - 1) / kWarps;
     s.groups_small = (s.cnt[0] + 31) / 32;
-    s.n_small_items = (s.groups_small + kWarps - 1) / kWarps;
-    s.total = s.n_cta + s.n_warp_items + s.n_small_items;
     return s;
 }
 
-// All CTAs pull work items of the level from one counter: first the CTA
-// chunks of bin 2 (largest first limits the tail), then warp items.
+// One level's expansion.  CTA chunks (bin 2) are pulled from a counter so
+// heavy vertices spread over whichever CTAs are free; warp items (bin 1
+// chunks, then bin 0 groups) are equal-sized by construction and dealt out
+// round robin over all warps of the grid, with no atomics or CTA barriers.
+// Each warp flushes its staged discoveries at the end; the CTA adds its
+// discovered-vertex count with one atomic.
 template <bool kBatch>
-__device__ void expand_level(const TraversalParams& P, const LevelShape& S, int level) {
+__device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
+                             int level) {
     __shared__ long long s_item;
+    __shared__ int s_disc;
     const int slot = level % 3, nslot = (level + 1) % 3;
     const int cur = level & 1, nxt = cur ^ 1;
     const int warp = threadIdx.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(&P.ctl[slot].work, 1u);
-        __syncthreads();
-        const long long item = s_item;
-        __syncthreads();
-        if (item >= S.total) break;
-        if (item < S.n_cta) {
-            expand_cta_chunk<kBatch>(P, cur, item, S.cnt[2], S.edges[2], level, nxt, nslot);
-        } else if (item < S.n_cta + S.n_warp_items) {
-            const long long c = (item - S.n_cta) * kWarps + warp;
-            if (c < S.chunks_warp)
-                expand_warp_chunk<kBatch>(P, cur, c, S.cnt[1], S.edges[1], level, nxt, nslot);
-        } else {
-            const long long g = (item - S.n_cta - S.n_warp_items) * kWarps + warp;
-            if (g < S.groups_small)
-                expand_small_group<kBatch>(P, cur, g, S.cnt[0], level, nxt, nslot);
+    int my_disc = 0;
+    if (threadIdx.x == 0) s_disc = 0;
+    __syncthreads();
+    if (L.n_cta > 0) {
+        for (;;) {
+            if (threadIdx.x == 0) s_item = (long long)atomicAdd(&P.ctl[slot].work, 1u);
+            __syncthreads();
+            const long long item = s_item;
+            __syncthreads();
+            if (item >= L.n_cta) break;
+            expand_cta_chunk<kBatch>(P, S, cur, item, L.cnt[2], L.edges[2], level, nxt, nslot,
+                                     my_disc);
         }
+    }
+    const long long nwarps = (long long)gridDim.x * kWarps;
+    const long long gw = (long long)blockIdx.x * kWarps + warp;
+    const long long witems = L.chunks_warp + L.groups_small;
+    for (long long it = gw; it < witems; it += nwarps) {
+        if (it < L.chunks_warp)
+            expand_warp_chunk<kBatch>(P, S, cur, it, L.cnt[1], L.edges[1], level, nxt, nslot,
+                                      my_disc);
+        else
+            expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt, nslot,
+                                       my_disc);
+    }
+    stage_flush_all<kBatch>(P, S, nxt, nslot);
+    if (!kBatch) {
+        const int wd = warp_incl_scan(my_disc);
+        if (lane_id() == 31 && wd > 0) atomicAdd(&s_disc, wd);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_disc > 0) atomicAdd(&P.ctl[nslot].discovered, (unsigned)s_disc);
     }
 }
 
@@ -491,19 +627,20 @@ __device__ void init_plain(const TraversalParams& P, long long tid, long long nt
     if (P.parent) fill_bytes(P.parent, P.n * 4, 0xff, tid, nthreads);
 }
 
-__device__ void seed_plain(const TraversalParams& P) {
+__device__ void seed_plain(const TraversalParams& P, Stage<false>& S) {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const bool l0 = threadIdx.x == 0;
     const int32_t root = P.old2new ? __ldg(P.old2new + P.root_caller) : P.root_caller;
-    long long deg = 0;
+    int deg = 0;
     if (l0) {
         P.visited[root >> 5] |= 1u << (root & 31);
         P.dist[P.root_caller] = 0;
         if (P.parent) P.parent[P.root_caller] = P.root_caller;
-        deg = __ldg(P.off + root + 1) - __ldg(P.off + root);
+        deg = (int)(__ldg(P.off + root + 1) - __ldg(P.off + root));
         P.ctl[0].discovered = 1u;
     }
-    enqueue_binned<false>(P, l0, root, deg, 0ull, 0, 0);
+    stage_push<false>(P, S, l0, root, deg, 0ull, 0, 0);
+    stage_flush_all<false>(P, S, 0, 0);
 }
 
 // Books the level that is about to be expanded; block 0, thread 0 only.
@@ -520,19 +657,23 @@ __device__ void book_level(const TraversalParams& P, const LevelShape& S, int le
 }
 
 // --------------------------------------------------------- plain kernels
-__global__ void __launch_bounds__(kBlock)
+template <int MB>
+__global__ void __launch_bounds__(kBlock, MB)
 bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
+    __shared__ Stage<false> s_stage[kWarps];
+    Stage<false>& S = s_stage[threadIdx.x >> 5];
+    stage_init(S);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     init_plain(P, tid, nthreads);
     if (grid_barrier(P)) {
-        seed_plain(P);
+        seed_plain(P, S);
         if (grid_barrier(P)) {
             for (int level = 0;; ++level) {
-                const LevelShape S = read_level(P, level);
-                book_level(P, S, level);
-                if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) break;
-                expand_level<false>(P, S, level);
+                const LevelShape L = read_level(P, level);
+                book_level(P, L, level);
+                if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) break;
+                expand_level<false>(P, S, L, level);
                 if (!grid_barrier(P)) break;
             }
         }
@@ -541,19 +682,23 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
 }
 
 // Host-loop variant: one launch per phase / level, no grid barrier.
-__global__ void __launch_bounds__(kBlock)
+template <int MB>
+__global__ void __launch_bounds__(kBlock, MB)
 bfs_plain_step(const __grid_constant__ TraversalParams P) {
+    __shared__ Stage<false> s_stage[kWarps];
+    Stage<false>& S = s_stage[threadIdx.x >> 5];
+    stage_init(S);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     if (P.phase == 0) {
         init_plain(P, tid, nthreads);
     } else if (P.phase == 1) {
-        seed_plain(P);
+        seed_plain(P, S);
     } else {
-        const LevelShape S = read_level(P, P.level);
-        book_level(P, S, P.level);
-        if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) return;
-        expand_level<false>(P, S, P.level);
+        const LevelShape L = read_level(P, P.level);
+        book_level(P, L, P.level);
+        if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
+        expand_level<false>(P, S, L, P.level);
     }
 }
 
@@ -583,7 +728,7 @@ __device__ __forceinline__ void write_lane_dist(const TraversalParams& P, int la
 
 // One warp seeds all roots: duplicates share one queue entry whose mask
 // holds every lane with that root.
-__device__ void seed_batch(const TraversalParams& P) {
+__device__ void seed_batch(const TraversalParams& P, Stage<true>& S) {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const unsigned lane = lane_id();
     long long reached = 0, edges = 0;
@@ -611,8 +756,9 @@ __device__ void seed_batch(const TraversalParams& P) {
             reached += 1;
             edges += deg;
         }
-        enqueue_binned<true>(P, first, r, deg, mask, 0, 0);
+        stage_push<true>(P, S, first, r, (int)deg, mask, 0, 0);
     }
+    stage_flush_all<true>(P, S, 0, 0);
     reached = warp_incl_scan(reached);
     edges = warp_incl_scan(edges);
     if (lane == 31) {
@@ -624,7 +770,7 @@ __device__ void seed_batch(const TraversalParams& P) {
 
 // Phase B of a batched level: lanes that reached v for the first time get
 // distance level + 1 and make v part of the next frontier with those lanes.
-__device__ void sweep_batch(const TraversalParams& P, int level, long long tid,
+__device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level, long long tid,
                             long long nthreads) {
     const int nslot = (level + 1) % 3, nxt = (level + 1) & 1;
     const unsigned lane = lane_id();
@@ -661,8 +807,10 @@ __device__ void sweep_batch(const TraversalParams& P, int level, long long tid,
                 if ((fresh >> li) & 1ull) write_lane_dist(P, li, cv, level + 1);
             }
         }
-        enqueue_binned<true>(P, fresh != 0ull, (int32_t)(v < P.n ? v : 0), deg, fresh, nxt, nslot);
+        stage_push<true>(P, S, fresh != 0ull, (int32_t)(v < P.n ? v : 0), (int)deg, fresh, nxt,
+                         nslot);
     }
+    stage_flush_all<true>(P, S, nxt, nslot);
     // per-warp totals
     my_pairs = warp_incl_scan(my_pairs);
     my_edges = warp_incl_scan(my_edges);
@@ -682,25 +830,29 @@ __device__ void book_batch_level(const TraversalParams& P, int level) {
     for (int i = 0; i < (int)(sizeof(LevelCtl) / 8); ++i) z[i] = 0ull;
 }
 
-__global__ void __launch_bounds__(kBlock)
+template <int MB>
+__global__ void __launch_bounds__(kBlock, MB)
 bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
+    __shared__ Stage<true> s_stage[kWarps];
+    Stage<true>& S = s_stage[threadIdx.x >> 5];
+    stage_init(S);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     init_batch(P, tid, nthreads);
     if (grid_barrier(P)) {
-        seed_batch(P);
+        seed_batch(P, S);
         if (grid_barrier(P)) {
             for (int level = 0;; ++level) {
-                const LevelShape S = read_level(P, level);
-                if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) break;
+                const LevelShape L = read_level(P, level);
+                if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) break;
                 if (P.dist_int8 && level + 1 > 126) {
                     if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(P, kDevDepth);
                     break;
                 }
                 book_batch_level(P, level);
-                expand_level<true>(P, S, level);
+                expand_level<true>(P, S, L, level);
                 if (!grid_barrier(P)) break;
-                sweep_batch(P, level, tid, nthreads);
+                sweep_batch(P, S, level, tid, nthreads);
                 if (!grid_barrier(P)) break;
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
                     if (__ldcg(reinterpret_cast<const unsigned long long*>(
@@ -713,24 +865,25 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
     kernel_exit(P);
 }
 
-__global__ void __launch_bounds__(kBlock)
+template <int MB>
+__global__ void __launch_bounds__(kBlock, MB)
 bfs_batch_step(const __grid_constant__ TraversalParams P) {
+    __shared__ Stage<true> s_stage[kWarps];
+    Stage<true>& S = s_stage[threadIdx.x >> 5];
+    stage_init(S);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     if (P.phase == 0) {
         init_batch(P, tid, nthreads);
     } else if (P.phase == 1) {
-        seed_batch(P);
+        seed_batch(P, S);
     } else if (P.phase == 2) {
-        const LevelShape S = read_level(P, P.level);
-        if (S.cnt[0] + S.cnt[1] + S.cnt[2] == 0) return;
+        const LevelShape L = read_level(P, P.level);
+        if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
         book_batch_level(P, P.level);
-        expand_level<true>(P, S, P.level);
+        expand_level<true>(P, S, L, P.level);
     } else {
-        sweep_batch(P, P.level, tid, nthreads);
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            // levels is finalised by the host from new_lanes in host-loop mode
-        }
+        sweep_batch(P, S, P.level, tid, nthreads);
     }
 }
 
@@ -783,10 +936,20 @@ __global__ void degree_bins_kernel(const int64_t* off, long long n, int t_small,
 }
 
 // -------------------------------------------------------- host wrappers
-const void* plain_persistent_fn() { return (const void*)bfs_plain_persistent; }
-const void* plain_step_fn() { return (const void*)bfs_plain_step; }
-const void* batch_persistent_fn() { return (const void*)bfs_batch_persistent; }
-const void* batch_step_fn() { return (const void*)bfs_batch_step; }
+// Kernels are instantiated for 2 and 3 resident CTAs per SM (register cap
+// 128 or 80); the graph's occupancy option picks one.
+const void* plain_persistent_fn(int mb) {
+    return mb >= 3 ? (const void*)bfs_plain_persistent<3> : (const void*)bfs_plain_persistent<2>;
+}
+const void* plain_step_fn(int mb) {
+    return mb >= 3 ? (const void*)bfs_plain_step<3> : (const void*)bfs_plain_step<2>;
+}
+const void* batch_persistent_fn(int mb) {
+    return mb >= 3 ? (const void*)bfs_batch_persistent<3> : (const void*)bfs_batch_persistent<2>;
+}
+const void* batch_step_fn(int mb) {
+    return mb >= 3 ? (const void*)bfs_batch_step<3> : (const void*)bfs_batch_step<2>;
+}
 
 cudaError_t launch_csr_check(const int64_t* off, const int32_t* col, long long n, long long nnz,
                              int* flags, int sms, cudaStream_t s) {

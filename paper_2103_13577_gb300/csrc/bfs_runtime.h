@@ -82,6 +82,7 @@ struct bfs_graph {
     int32_t debug_stall = 0;
     long long timeout_ns = 2000000000ll;
     int32_t use_match_any = 0;
+    int32_t min_blocks = 2;           // resident CTAs per SM the kernels are built for
     std::mutex mu;
 };
 

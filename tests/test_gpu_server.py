@@ -35,16 +35,19 @@ def test_mixed_queries_match_alone(setup):
     srv = bfs.Server(ctx, 512 << 20, num_streams=3)
     gids = [srv.add_graph(g) for _, _, g in graphs]
     rng = np.random.default_rng(0)
-    queries = []
+    plan = []
     for i in range(150):
         gi = int(rng.integers(0, len(graphs)))
         off, col, _ = graphs[gi]
         root = int(graphgen.pick_roots(off, 1, seed=1000 + i)[0])
-        out = np.full(len(off) - 1, -7, dtype=np.int32)
-        t = srv.submit(gids[gi], root, out)
-        queries.append((gi, root, out, t))
-        if i % 10 == 0:
-            time.sleep(0.001)  # let some launches start while more arrive
+        plan.append((gi, root, np.full(len(off) - 1, -7, dtype=np.int32)))
+    queries = []
+    # first wave in a tight loop (queries pile up behind the busy slots and
+    # get packed), second wave trickles in while the first is on the device
+    for i, (gi, root, out) in enumerate(plan):
+        queries.append((gi, root, out, srv.submit(gids[gi], root, out)))
+        if i >= 100 and i % 10 == 0:
+            time.sleep(0.001)
     for gi, root, out, t in queries:
         assert srv.wait(t, 30_000_000) == bfs.BFS_OK
         off, col, _ = graphs[gi]
