@@ -1,0 +1,387 @@
+"""Benchmark: plain single-source BFS GTEPS on a Kronecker graph.
+
+Workload: undirected Kronecker graph, scale 22, edge factor 16 (initiator
+0.57/0.19/0.19/0.05, seeded permutation, no self-loops or duplicates,
+int64 offsets + int32 columns), 64 seeded roots of degree >= 1 run one
+after another.  One step = the 64 single-source traversals (init, level
+loop with degree-binned expansion, visited test-and-set, dist/parent
+writes and frontier compaction -- the whole per-GPU level step).
+
+Metric: GTEPS per root = m_c / t (m_c = adjacency entries scanned from
+that root, t = that root's traversal time on the device), aggregated by
+the harmonic mean over the 64 roots.  Under torchrun each rank traverses
+its own 64 roots on its own copy of the graph (weak scaling, no
+collective); root i's job throughput is the sum over ranks of m_c divided
+by the slowest rank's time for root i.
+
+Also reported: e2e (the same metric through bfs_run with host output
+buffers, result copies inside the timed region), the roofline of the
+traversal kernel against the measured HBM bandwidth, the CPU oracle on a
+bounded sample of roots, a 64-root batched launch on the same graph, and
+SM clocks sampled during the timed region.
+
+--impl reference times the CPU oracle (serial FIFO BFS) on the host cores
+for the same metric: each step traverses a bounded sample of the roots.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+SCALE, EDGE_FACTOR, GRAPH_SEED, ROOT_SEED, NROOTS = 22, 16, 22, 3, 64
+METRIC = "BFS GTEPS (hmean over 64 roots) plain vs 64-root batched; query p50/p99 latency"
+WORKLOAD = "kronecker_s22_ef16_plain_64roots"
+KERNEL_SRC = os.path.join(ROOT, "paper_2103_13577_gb300", "csrc", "bfs_kernels.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_plain_persistent_kron_s22_traffic.json")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def hmean(x):
+    x = np.asarray(x, dtype=np.float64)
+    return float(len(x) / np.sum(1.0 / x))
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_hash():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu capture, or None when the
+    kernel source changed since the capture."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+        if rec.get("kernel_sha256_16") != kernel_hash():
+            return None
+        return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clocks and throttle reasons."""
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_workload(rank):
+    import graphgen
+    off, col = graphgen.kronecker(SCALE, EDGE_FACTOR, seed=GRAPH_SEED)
+    roots = graphgen.pick_roots(off, NROOTS, seed=ROOT_SEED + 7919 * rank)
+    return off, col, roots
+
+
+# ---------------------------------------------------------------- oracle
+def run_oracle_sample(off, col, roots, budget_s):
+    """Serial oracle over as many roots as fit in budget_s (at least one)."""
+    import oracle
+    gteps, used = [], []
+    t_start = time.perf_counter()
+    for r in roots:
+        t0 = time.perf_counter()
+        _, _, info = oracle.bfs(off, col, int(r))
+        dt = time.perf_counter() - t0
+        gteps.append(info["edges_scanned"] / dt / 1e9)
+        used.append(int(r))
+        if time.perf_counter() - t_start > budget_s:
+            break
+    return gteps, used
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    off, col, roots = make_workload(0)
+    per_step = max(1, env_int("BFS_REF_ROOTS_PER_STEP", 2))
+    i = 0
+    for _ in range(args.warmup):
+        run_oracle_sample(off, col, roots[i:i + 1], 0)
+        i = (i + 1) % len(roots)
+    gteps, step_ms = [], []
+    for _ in range(args.steps):
+        sel = [roots[(i + j) % len(roots)] for j in range(per_step)]
+        i = (i + per_step) % len(roots)
+        t0 = time.perf_counter()
+        g, _ = run_oracle_sample(off, col, sel, 1e9)
+        step_ms.append((time.perf_counter() - t0) * 1e3)
+        gteps.extend(g)
+    value = hmean(gteps)
+    sample = f"{per_step} of the 64 roots per step, serial FIFO BFS on one host core"
+    line = {
+        "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "graph": f"kronecker scale {SCALE} edge factor {EDGE_FACTOR}",
+                   "vertices": len(off) - 1, "directed_entries": int(len(col)), "roots": NROOTS},
+        "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist_mod
+
+    import paper_2103_13577_gb300 as bfs
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    off, col, roots = make_workload(rank)
+    n = len(off) - 1
+    ctx = bfs.Context(local_rank)
+    g = bfs.Graph(ctx, off, col)
+    if args.bins:
+        g.set_bins(*[int(x) for x in args.bins.split(",")])
+    if args.ctas_per_sm:
+        g.set_option(bfs.BFS_OPT_CTAS_PER_SM, args.ctas_per_sm)
+    stream = torch.cuda.current_stream(dev)
+    dist = torch.empty(n, dtype=torch.int32, device=dev)
+    parent = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist_mod.barrier()
+
+    # per-root m_c and n_c from the device's own counters (untimed pass)
+    m_c = np.zeros(NROOTS, dtype=np.int64)
+    n_c = np.zeros(NROOTS, dtype=np.int64)
+    for i, r in enumerate(roots):
+        g.run(int(r), dist, parent, stream=stream)
+        st = g.sync(stream)
+        m_c[i], n_c[i] = st["edges_scanned"], st["reached"]
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(NROOTS + 1)] for _ in range(args.steps)]
+    for _ in range(args.warmup):
+        for r in roots:
+            g.run(int(r), dist, parent, stream=stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.25)
+    for s in range(args.steps):
+        ev[s][0].record(stream)
+        for i, r in enumerate(roots):
+            g.run(int(r), dist, parent, stream=stream)
+            ev[s][i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    root_ms = np.array([[ev[s][i].elapsed_time(ev[s][i + 1]) for i in range(NROOTS)]
+                        for s in range(args.steps)])
+    step_ms = np.array([ev[s][0].elapsed_time(ev[s][NROOTS]) for s in range(args.steps)])
+    st = g.sync(stream)
+    assert st["status"] == 0
+
+    # whole-job aggregation over ranks: root i -> sum of m_c / max time
+    t_root = root_ms.mean(axis=0)
+    if world > 1:
+        t_all = torch.tensor(t_root, dtype=torch.float64, device=dev)
+        dist_mod.all_reduce(t_all, op=dist_mod.ReduceOp.MAX)
+        m_all = torch.tensor(m_c, dtype=torch.float64, device=dev)
+        dist_mod.all_reduce(m_all, op=dist_mod.ReduceOp.SUM)
+        s_all = torch.tensor([step_ms.mean()], dtype=torch.float64, device=dev)
+        dist_mod.all_reduce(s_all, op=dist_mod.ReduceOp.MAX)
+        t_job, m_job, ms_step = t_all.cpu().numpy(), m_all.cpu().numpy(), float(s_all.item())
+    else:
+        t_job, m_job, ms_step = t_root, m_c.astype(np.float64), float(step_ms.mean())
+    gteps_root = m_job / (t_job * 1e-3) / 1e9
+    value = hmean(gteps_root)
+
+    # e2e: the public call with host outputs (copies inside the timed region)
+    h_dist = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
+    h_par = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
+    for r in roots[:3]:
+        g.run(int(r), h_dist, h_par)
+    barrier()
+    e2e_ms = np.zeros(NROOTS)
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        for i, r in enumerate(roots):
+            t0 = time.perf_counter()
+            g.run(int(r), h_dist, h_par)
+            e2e_ms[i] += (time.perf_counter() - t0) * 1e3
+    e2e_ms /= e2e_steps
+    if world > 1:
+        t_e = torch.tensor(e2e_ms, dtype=torch.float64, device=dev)
+        dist_mod.all_reduce(t_e, op=dist_mod.ReduceOp.MAX)
+        e2e_ms = t_e.cpu().numpy()
+    e2e_value = hmean(m_job / (e2e_ms * 1e-3) / 1e9)
+
+    # 64-root batched launch on the same graph (one persistent launch)
+    bd = torch.empty((NROOTS, n), dtype=torch.int32, device=dev)
+    for _ in range(2):
+        g.run_batch(roots, bd, stream=stream)
+    bst = g.batch_sync(stream)
+    bev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    reps = 3
+    bev[0].record(stream)
+    for _ in range(reps):
+        g.run_batch(roots, bd, stream=stream)
+    bev[1].record(stream)
+    bst = g.batch_sync(stream)
+    batch_ms = bev[0].elapsed_time(bev[1]) / reps
+    batch_gteps = bst["edges_scanned"] / (batch_ms * 1e-3) / 1e9
+
+    # roofline of the traversal kernel (one launch per root)
+    peak, peak_kind = measured_hbm_peak()
+    alg_bytes = 4.0 * m_c + 32.0 * n_c + 8.125 * n
+    achieved = float(np.mean(alg_bytes / (t_root * 1e-3)) / 1e9)
+    traffic = recorded_traffic()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gts, used = run_oracle_sample(off, col, roots, args.cpu_budget)
+        cpu = {"value": hmean(gts), "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"{len(used)} of the 64 roots, serial FIFO BFS on one host core"}
+
+    if rank == 0:
+        info = g.info()
+        line = {
+            "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD,
+                       "graph": f"kronecker scale {SCALE} edge factor {EDGE_FACTOR} "
+                                "A/B/C=0.57/0.19/0.19, permuted, symmetric, deduplicated",
+                       "vertices": n, "directed_entries": int(len(col)), "roots": NROOTS,
+                       "root_seed": ROOT_SEED, "graph_seed": GRAPH_SEED,
+                       "bins": [info["t_small"], info["t_large"], info["chunk_warp"], info["chunk_cta"]],
+                       "relabelled": bool(info["relabelled"]),
+                       "l2": "inputs larger than L2 (column array %.0f MB > 129 MB)" % (len(col) * 4 / 1e6),
+                       "parallelism": f"replicas x{world}"},
+            "aggregate_gteps": float(m_job.sum() / (t_job.sum() * 1e-3) / 1e9),
+            "root_ms_median": float(np.median(t_job)),
+            "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": 4 * NROOTS,
+                    "d2h_bytes_per_step": 2 * 4 * n * NROOTS},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "bfs_plain_persistent",
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"
+                         if peak_kind == "measured" else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": float(alg_bytes.mean())},
+            "cpu_baseline": cpu,
+            "batched": {"roots": NROOTS, "ms": batch_ms, "gteps": batch_gteps,
+                        "edges": int(bst["edges_scanned"]), "levels": int(bst["levels"]),
+                        "speedup_vs_plain_step": ms_step / batch_ms},
+            "clocks": clk,
+            "gpu_launches": int(args.steps * NROOTS),
+        }
+        print(json.dumps(line), flush=True)
+    g.close()
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--bins", default="", help="t_small,t_large,chunk_warp,chunk_cta")
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = env_int("RANK", 0)
+    world = env_int("WORLD_SIZE", 1)
+    local_rank = env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist_mod
+        torch.cuda.set_device(local_rank)
+        dist_mod.init_process_group("nccl")
+    gpu_arm(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist_mod
+        dist_mod.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -133,132 +133,164 @@ __device__ void kernel_exit(const TraversalParams& P) {
 }
 
 // --------------------------------------------------------------- enqueue
-// Discovered vertices are staged per warp in shared memory and appended to
-// the next frontier 64 at a time: one 64-bit atomicAdd per bin reserves
-// both the queue slots and the edge range of the whole group (the bin
-// counter packs entries << 34 | edge prefix), so the hot counters see one
-// atomic per 64 discoveries instead of one per warp step.
+// Claimed vertices are staged per warp in shared memory and appended to the
+// next frontier 64 at a time.  The flush does the per-vertex work that
+// needs random reads (degree from the row offsets, caller numbering) for
+// the whole group at once, writes the distances and parents, bins the
+// group by degree, and reserves queue slots and edge ranges with one 64-bit
+// atomicAdd per bin (the bin counter packs entries << 34 | edge prefix).
 constexpr int kStageCap = 64;
 
 template <bool kBatch>
 struct Stage {
-    int32_t v[kBins][kStageCap];
-    int32_t deg[kBins][kStageCap];
-    unsigned long long mask[kBatch ? kBins : 1][kBatch ? kStageCap : 1];
-    int cnt[kBins];
+    int32_t u[kStageCap];
+    int32_t v[kBatch ? 1 : kStageCap];                 // plain: parent of u
+    unsigned long long mask[kBatch ? kStageCap : 1];   // batched: new lanes of u
+    int cnt;
+    unsigned long long edges;                          // batched: sum deg * lanes
 };
 
-// Warp-collective: appends the staged entries of bin b to the next frontier.
+// Warp-collective flush of the staged entries into the next frontier.
 template <bool kBatch>
-__device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>& S, int b,
+__device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>& S, int level,
                                          int nxt, int nslot) {
     const unsigned lane = lane_id();
-    const int n = S.cnt[b];
+    const int n = S.cnt;
     if (n == 0) return;
-    const int i0 = (int)lane, i1 = (int)lane + 32;
-    const long long d0 = i0 < n ? S.deg[b][i0] : 0, d1 = i1 < n ? S.deg[b][i1] : 0;
-    const long long incl0 = warp_incl_scan(d0);
-    const long long tot0 = __shfl_sync(FULL_MASK, incl0, 31);
-    const long long incl1 = warp_incl_scan(d1) + tot0;
-    const long long tot = __shfl_sync(FULL_MASK, incl1, 31);
-    unsigned long long basep = 0ull;
-    if (lane == 0)
-        basep = atomicAdd(&P.ctl[nslot].packed[b],
-                          ((unsigned long long)n << kCountShift) + (unsigned long long)tot);
-    basep = __shfl_sync(FULL_MASK, basep, 0);
-    const BinQueue& Q = P.q[nxt][b];
-    const long long C = (b == 1) ? P.chunk_warp : P.chunk_cta;
+    int32_t u[2];
+    long long deg[2];
+    int bin[2];
+    uint64_t mask[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int i = h ? i1 : i0;
-        if (i >= n) continue;
-        const long long d = h ? d1 : d0;
-        const long long pos = (long long)(basep >> kCountShift) + i;
-        const long long eo = (long long)(basep & kEdgeMask) + (h ? incl1 : incl0) - d;
-        if (pos >= Q.cap) {
-            raise_status(P, kDevOverflow);
-            continue;
+        const int i = (int)lane + 32 * h;
+        u[h] = 0;
+        deg[h] = 0;
+        mask[h] = 0ull;
+        if (i < n) {
+            u[h] = S.u[i];
+            deg[h] = __ldg(P.off + u[h] + 1) - __ldg(P.off + u[h]);
+            if (kBatch) mask[h] = S.mask[kBatch ? i : 0];
         }
-        Q.v[pos] = S.v[b][i];
-        if (kBatch) Q.mask[pos] = S.mask[kBatch ? b : 0][kBatch ? i : 0];
-        if (b > 0) {
-            Q.eoff[pos] = eo;
-            for (long long c = (eo + C - 1) / C; c * C < eo + d; ++c) {
-                if (c < Q.chunk_cap) Q.chunk[c] = (int32_t)pos;
-                else raise_status(P, kDevOverflow);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = (int)lane + 32 * h;
+        if (i >= n) continue;
+        if constexpr (kBatch) {
+            atomicAdd(&S.edges, (unsigned long long)(deg[h] * __popcll(mask[h])));
+        } else {
+            const int32_t vv = S.v[i];
+            const int32_t cu = P.new2old ? __ldg(P.new2old + u[h]) : u[h];
+            const int32_t cv = P.new2old ? __ldg(P.new2old + vv) : vv;
+            P.dist[cu] = level + 1;
+            if (P.parent) P.parent[cu] = cv;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = (int)lane + 32 * h;
+        bin[h] = (i >= n || deg[h] <= 0) ? -1
+                 : (deg[h] < P.t_small ? 0 : (deg[h] < P.t_large ? 1 : 2));
+    }
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        const unsigned m0 = __ballot_sync(FULL_MASK, bin[0] == b);
+        const unsigned m1 = __ballot_sync(FULL_MASK, bin[1] == b);
+        const int c0 = __popc(m0), cnt = c0 + __popc(m1);
+        if (cnt == 0) continue;
+        const long long d0 = bin[0] == b ? deg[0] : 0ll, d1 = bin[1] == b ? deg[1] : 0ll;
+        const long long incl0 = warp_incl_scan(d0);
+        const long long tot0 = __shfl_sync(FULL_MASK, incl0, 31);
+        const long long incl1 = warp_incl_scan(d1) + tot0;
+        const long long tot = __shfl_sync(FULL_MASK, incl1, 31);
+        unsigned long long basep = 0ull;
+        if (lane == 0)
+            basep = atomicAdd(&P.ctl[nslot].packed[b],
+                              ((unsigned long long)cnt << kCountShift) + (unsigned long long)tot);
+        basep = __shfl_sync(FULL_MASK, basep, 0);
+        const BinQueue& Q = P.q[nxt][b];
+        const long long C = (b == 1) ? P.chunk_warp : P.chunk_cta;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (bin[h] != b) continue;
+            const long long rank = h ? c0 + __popc(m1 & lanemask_lt()) : __popc(m0 & lanemask_lt());
+            const long long pos = (long long)(basep >> kCountShift) + rank;
+            const long long d = h ? d1 : d0;
+            const long long eo = (long long)(basep & kEdgeMask) + (h ? incl1 : incl0) - d;
+            if (pos >= Q.cap) {
+                raise_status(P, kDevOverflow);
+                continue;
+            }
+            Q.v[pos] = u[h];
+            if (kBatch) Q.mask[pos] = mask[h];
+            if (b > 0) {
+                Q.eoff[pos] = eo;
+                for (long long c = (eo + C - 1) / C; c * C < eo + d; ++c) {
+                    if (c < Q.chunk_cap) Q.chunk[c] = (int32_t)pos;
+                    else raise_status(P, kDevOverflow);
+                }
             }
         }
     }
     __syncwarp();
-    if (lane == 0) S.cnt[b] = 0;
+    if (lane == 0) S.cnt = 0;
     __syncwarp();
 }
 
-// Warp-collective: lanes with ok stage (u, deg, mask) into the bin of deg.
-// Vertices without out-edges are never queued (nothing to expand).
+// Warp-collective: lanes with ok stage u (with its parent v, or its new
+// lanes mask).
 template <bool kBatch>
 __device__ __forceinline__ void stage_push(const TraversalParams& P, Stage<kBatch>& S, bool ok,
-                                           int32_t u, int deg, uint64_t mask, int nxt, int nslot) {
-    ok = ok && deg > 0;
-    const int bin = deg < P.t_small ? 0 : (deg < P.t_large ? 1 : 2);
-    const unsigned lane = lane_id();
-#pragma unroll
-    for (int b = 0; b < kBins; ++b) {
-        const bool mine = ok && bin == b;
-        const unsigned m = __ballot_sync(FULL_MASK, mine);
-        if (m == 0u) continue;
-        int n0 = S.cnt[b];
-        const int k = __popc(m);
-        if (n0 + k > kStageCap) {
-            stage_flush<kBatch>(P, S, b, nxt, nslot);
-            n0 = 0;
-        }
-        if (mine) {
-            const int i = n0 + __popc(m & lanemask_lt());
-            S.v[b][i] = u;
-            S.deg[b][i] = deg;
-            if (kBatch) S.mask[kBatch ? b : 0][kBatch ? i : 0] = mask;
-        }
-        __syncwarp();
-        if (lane == 0) S.cnt[b] = n0 + k;
-        __syncwarp();
+                                           int32_t u, int32_t v, uint64_t mask, int level,
+                                           int nxt, int nslot) {
+    const unsigned m = __ballot_sync(FULL_MASK, ok);
+    if (m == 0u) return;
+    int n0 = S.cnt;
+    const int k = __popc(m);
+    if (n0 + k > kStageCap) {
+        stage_flush<kBatch>(P, S, level, nxt, nslot);
+        n0 = 0;
     }
-}
-
-template <bool kBatch>
-__device__ __forceinline__ void stage_flush_all(const TraversalParams& P, Stage<kBatch>& S,
-                                                int nxt, int nslot) {
-#pragma unroll
-    for (int b = 0; b < kBins; ++b) stage_flush<kBatch>(P, S, b, nxt, nslot);
+    if (ok) {
+        const int i = n0 + __popc(m & lanemask_lt());
+        S.u[i] = u;
+        if constexpr (kBatch) S.mask[i] = mask;
+        else S.v[i] = v;
+    }
+    __syncwarp();
+    if (lane_id() == 0) S.cnt = n0 + k;
+    __syncwarp();
 }
 
 template <bool kBatch>
 __device__ __forceinline__ void stage_init(Stage<kBatch>& S) {
-    if (lane_id() < (unsigned)kBins) S.cnt[lane_id()] = 0;
+    if (lane_id() == 0) {
+        S.cnt = 0;
+        S.edges = 0ull;
+    }
     __syncwarp();
 }
 
 // ----------------------------------------------------------------- visits
 // K edges per lane at once: all K visited-bitmap probes are issued before
 // any result is used, then the atomics, so a warp keeps K random accesses
-// in flight instead of one.
+// in flight instead of one.  Winners only go to the warp's stage.
 template <int K>
 __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<false>& S,
-                                              const bool (&ok)[K], const int32_t (&u)[K],
+                                              unsigned okm, const int32_t (&u)[K],
                                               const int32_t (&v)[K], int level, int nxt,
                                               int nslot, int& my_disc) {
     uint32_t w[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) w[j] = ok[j] ? P.visited[u[j] >> 5] : 0xffffffffu;
-    bool win[K];
-    bool any = false;
+    for (int j = 0; j < K; ++j) w[j] = ((okm >> j) & 1u) ? P.visited[u[j] >> 5] : 0xffffffffu;
+    unsigned winm = 0u;
     if (P.use_match_any) {
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const uint32_t bit = 1u << (u[j] & 31);
             const bool need = (w[j] & bit) == 0u;
             const unsigned needm = __ballot_sync(FULL_MASK, need);
-            win[j] = false;
             if (need) {
                 const unsigned peers = __match_any_sync(needm, u[j] >> 5);
                 const uint32_t bits = __reduce_or_sync(peers, bit);
@@ -267,45 +299,25 @@ __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<fa
                 if ((int)lane_id() == leader) old = atomicOr(P.visited + (u[j] >> 5), bits);
                 old = __shfl_sync(peers, old, leader);
                 const unsigned same = __match_any_sync(peers, u[j]);
-                win[j] = ((old & bit) == 0u) && ((int)lane_id() == __ffs(same) - 1);
+                if (((old & bit) == 0u) && ((int)lane_id() == __ffs(same) - 1)) winm |= 1u << j;
             }
-            any |= win[j];
         }
     } else {
-        uint32_t old[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             const uint32_t bit = 1u << (u[j] & 31);
-            old[j] = bit;
-            if ((w[j] & bit) == 0u) old[j] = atomicOr(P.visited + (u[j] >> 5), bit);
+            if ((w[j] & bit) == 0u) w[j] = atomicOr(P.visited + (u[j] >> 5), bit);
+            else w[j] = bit;
         }
 #pragma unroll
-        for (int j = 0; j < K; ++j) {
-            win[j] = (old[j] & (1u << (u[j] & 31))) == 0u;
-            any |= win[j];
-        }
+        for (int j = 0; j < K; ++j)
+            if ((w[j] & (1u << (u[j] & 31))) == 0u) winm |= 1u << j;
     }
-    if (__ballot_sync(FULL_MASK, any) == 0u) return;
-    long long b0[K], b1[K];
+    if (__ballot_sync(FULL_MASK, winm != 0u) == 0u) return;
+    my_disc += __popc(winm);
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        b0[j] = 0;
-        b1[j] = 0;
-        if (win[j]) {
-            b0[j] = __ldg(P.off + u[j]);
-            b1[j] = __ldg(P.off + u[j] + 1);
-            const int32_t cu = P.new2old ? __ldg(P.new2old + u[j]) : u[j];
-            const int32_t cv = P.new2old ? __ldg(P.new2old + v[j]) : v[j];
-            P.dist[cu] = level + 1;
-            if (P.parent) P.parent[cu] = cv;
-            ++my_disc;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        if (__ballot_sync(FULL_MASK, win[j]) == 0u) continue;
-        stage_push<false>(P, S, win[j], u[j], (int)(b1[j] - b0[j]), 0ull, nxt, nslot);
-    }
+    for (int j = 0; j < K; ++j)
+        stage_push<false>(P, S, (winm >> j) & 1u, u[j], v[j], 0ull, level, nxt, nslot);
 }
 
 // Batched traversal, phase A: OR the lanes of the frontier entry that u has
@@ -313,12 +325,12 @@ __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<fa
 // value is a safe filter; next[u] is read first so that lanes already
 // present skip the atomic (a fire-and-forget red.or otherwise).
 template <int K>
-__device__ __forceinline__ void visit_batch_k(const TraversalParams& P, const bool (&ok)[K],
+__device__ __forceinline__ void visit_batch_k(const TraversalParams& P, unsigned okm,
                                               const int32_t (&u)[K],
                                               const uint64_t (&mask)[K]) {
     uint64_t m[K];
 #pragma unroll
-    for (int j = 0; j < K; ++j) m[j] = ok[j] ? (mask[j] & ~P.lane_visited[u[j]]) : 0ull;
+    for (int j = 0; j < K; ++j) m[j] = ((okm >> j) & 1u) ? (mask[j] & ~P.lane_visited[u[j]]) : 0ull;
     uint64_t nx[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) nx[j] = m[j] ? P.lane_next[u[j]] : ~0ull;
@@ -330,12 +342,12 @@ __device__ __forceinline__ void visit_batch_k(const TraversalParams& P, const bo
 }
 
 template <bool kBatch, int K>
-__device__ __forceinline__ void visit_k(const TraversalParams& P, Stage<kBatch>& S,
-                                        const bool (&ok)[K], const int32_t (&u)[K],
-                                        const int32_t (&v)[K], const uint64_t (&mask)[K],
-                                        int level, int nxt, int nslot, int& my_disc) {
-    if constexpr (kBatch) visit_batch_k<K>(P, ok, u, mask);
-    else visit_plain_k<K>(P, S, ok, u, v, level, nxt, nslot, my_disc);
+__device__ __forceinline__ void visit_k(const TraversalParams& P, Stage<kBatch>& S, unsigned okm,
+                                        const int32_t (&u)[K], const int32_t (&v)[K],
+                                        const uint64_t (&mask)[K], int level, int nxt, int nslot,
+                                        int& my_disc) {
+    if constexpr (kBatch) visit_batch_k<K>(P, okm, u, mask);
+    else visit_plain_k<K>(P, S, okm, u, v, level, nxt, nslot, my_disc);
 }
 
 // ------------------------------------------------------------ expansion
@@ -351,6 +363,9 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
                                                long long wstride, int& my_disc) {
     const unsigned lane = lane_id();
     const long long a4 = a & ~3ll;
+    const int lo = (int)(a - a4);                 // valid entries: [lo, hi) relative to a4
+    const int hi = (int)(b - a4);
+    const int32_t* colp = P.col + a4;
     int32_t vv[8];
     uint64_t mm[8];
 #pragma unroll
@@ -358,30 +373,34 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
         vv[j] = v;
         mm[j] = mask;
     }
-    if (wbase == 0 && wstride == 256 && b - a4 <= 128) {
-        const long long p0 = a4 + 4 * lane;
+    if (wbase == 0 && wstride == 256 && hi <= 128) {
+        const int r0 = 4 * (int)lane;
         int4 x0 = make_int4(0, 0, 0, 0);
-        if (p0 < b) x0 = __ldcs(reinterpret_cast<const int4*>(P.col + p0));
-        const bool ok[4] = {p0 >= a && p0 < b, p0 + 1 >= a && p0 + 1 < b,
-                            p0 + 2 >= a && p0 + 2 < b, p0 + 3 >= a && p0 + 3 < b};
+        if (r0 < hi) x0 = __ldcs(reinterpret_cast<const int4*>(colp + r0));
+        unsigned okm = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (r0 + j >= lo && r0 + j < hi) okm |= 1u << j;
         const int32_t u[4] = {x0.x, x0.y, x0.z, x0.w};
         const int32_t v4[4] = {v, v, v, v};
         const uint64_t m4[4] = {mask, mask, mask, mask};
-        visit_k<kBatch, 4>(P, S, ok, u, v4, m4, level, nxt, nslot, my_disc);
+        visit_k<kBatch, 4>(P, S, okm, u, v4, m4, level, nxt, nslot, my_disc);
         return;
     }
-    for (long long pw = a4 + wbase; pw < b; pw += wstride) {
-        const long long p0 = pw + 4 * lane;
-        const long long p1 = p0 + 128;
+    for (int rw = (int)wbase; rw < hi; rw += (int)wstride) {
+        const int r0 = rw + 4 * (int)lane;
+        const int r1 = r0 + 128;
         int4 x0 = make_int4(0, 0, 0, 0), x1 = make_int4(0, 0, 0, 0);
-        if (p0 < b) x0 = __ldcs(reinterpret_cast<const int4*>(P.col + p0));
-        if (p1 < b) x1 = __ldcs(reinterpret_cast<const int4*>(P.col + p1));
-        const bool ok[8] = {p0 >= a && p0 < b,         p0 + 1 >= a && p0 + 1 < b,
-                            p0 + 2 >= a && p0 + 2 < b, p0 + 3 >= a && p0 + 3 < b,
-                            p1 >= a && p1 < b,         p1 + 1 >= a && p1 + 1 < b,
-                            p1 + 2 >= a && p1 + 2 < b, p1 + 3 >= a && p1 + 3 < b};
+        if (r0 < hi) x0 = __ldcs(reinterpret_cast<const int4*>(colp + r0));
+        if (r1 < hi) x1 = __ldcs(reinterpret_cast<const int4*>(colp + r1));
+        unsigned okm = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (r0 + j >= lo && r0 + j < hi) okm |= 1u << j;
+            if (r1 + j >= lo && r1 + j < hi) okm |= 1u << (4 + j);
+        }
         const int32_t u[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        visit_k<kBatch, 8>(P, S, ok, u, vv, mm, level, nxt, nslot, my_disc);
+        visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
     }
 }
 
@@ -410,7 +429,7 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
     const int excl = incl - deg;
     const int total = __shfl_sync(FULL_MASK, incl, 31);
     for (int e0 = 0; e0 < total; e0 += 256) {
-        bool ok[8];
+        unsigned okm = 0u;
         int32_t u[8], vv[8];
         uint64_t mm[8];
 #pragma unroll
@@ -426,10 +445,13 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
             const int xo = __shfl_sync(FULL_MASK, excl, o);
             vv[j] = __shfl_sync(FULL_MASK, v, o);
             mm[j] = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, o) : 0ull;
-            ok[j] = e < total;
-            u[j] = ok[j] ? __ldcs(P.col + bo + (e - xo)) : 0;
+            u[j] = 0;
+            if (e < total) {
+                okm |= 1u << j;
+                u[j] = __ldcs(P.col + bo + (e - xo));
+            }
         }
-        visit_k<kBatch, 8>(P, S, ok, u, vv, mm, level, nxt, nslot, my_disc);
+        visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
     }
 }
 
@@ -582,7 +604,7 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
             expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt, nslot,
                                        my_disc);
     }
-    stage_flush_all<kBatch>(P, S, nxt, nslot);
+    stage_flush<kBatch>(P, S, level, nxt, nslot);
     if (!kBatch) {
         const int wd = warp_incl_scan(my_disc);
         if (lane_id() == 31 && wd > 0) atomicAdd(&s_disc, wd);
@@ -639,8 +661,11 @@ __device__ void seed_plain(const TraversalParams& P, Stage<false>& S) {
         deg = (int)(__ldg(P.off + root + 1) - __ldg(P.off + root));
         P.ctl[0].discovered = 1u;
     }
-    stage_push<false>(P, S, l0, root, deg, 0ull, 0, 0);
-    stage_flush_all<false>(P, S, 0, 0);
+    (void)deg;
+    // the root's distance and parent are already set; stage it with level
+    // -1 would rewrite them, so enqueue through the flush with its own values
+    stage_push<false>(P, S, l0, root, P.old2new ? root : P.root_caller, 0ull, -1, 0, 0);
+    stage_flush<false>(P, S, -1, 0, 0);
 }
 
 // Books the level that is about to be expanded; block 0, thread 0 only.
@@ -731,13 +756,11 @@ __device__ __forceinline__ void write_lane_dist(const TraversalParams& P, int la
 __device__ void seed_batch(const TraversalParams& P, Stage<true>& S) {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const unsigned lane = lane_id();
-    long long reached = 0, edges = 0;
     for (int base = 0; base < P.nlanes; base += 32) {
         const int i = base + (int)lane;
         bool first = false;
         int32_t r = 0;
         uint64_t mask = 0ull;
-        long long deg = 0;
         if (i < P.nlanes) {
             const int32_t cr = P.roots[i];
             first = true;
@@ -749,23 +772,18 @@ __device__ void seed_batch(const TraversalParams& P, Stage<true>& S) {
             }
             r = P.old2new ? __ldg(P.old2new + cr) : cr;
             write_lane_dist(P, i, cr, 0);
-            deg = __ldg(P.off + r + 1) - __ldg(P.off + r);
-            if (first) {
-                P.lane_visited[r] = mask;
-            }
-            reached += 1;
-            edges += deg;
+            if (first) P.lane_visited[r] = mask;
         }
-        stage_push<true>(P, S, first, r, (int)deg, mask, 0, 0);
+        stage_push<true>(P, S, first, r, 0, mask, -1, 0, 0);
     }
-    stage_flush_all<true>(P, S, 0, 0);
-    reached = warp_incl_scan(reached);
-    edges = warp_incl_scan(edges);
-    if (lane == 31) {
-        P.stats->reached = reached;
-        P.stats->edges = edges;
+    stage_flush<true>(P, S, -1, 0, 0);
+    if (lane == 0) {
+        P.stats->reached = P.nlanes;
+        P.stats->edges = (long long)S.edges;
         P.stats->levels = 1;
+        S.edges = 0ull;
     }
+    __syncwarp();
 }
 
 // Phase B of a batched level: lanes that reached v for the first time get
@@ -774,11 +792,10 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
                             long long nthreads) {
     const int nslot = (level + 1) % 3, nxt = (level + 1) & 1;
     const unsigned lane = lane_id();
-    long long my_pairs = 0, my_edges = 0;
+    long long my_pairs = 0;
     const long long nround = (P.n + 31) / 32 * 32;  // warp-uniform trip count
     for (long long v = tid; v < nround; v += nthreads) {
         uint64_t fresh = 0ull;
-        long long deg = 0;
         if (v < P.n) {
             const uint64_t nx = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_next) + v);
             if (nx != 0ull) {
@@ -788,10 +805,7 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
                 P.lane_next[v] = 0ull;
                 if (fresh != 0ull) {
                     P.lane_visited[v] = vis | fresh;
-                    deg = __ldg(P.off + v + 1) - __ldg(P.off + v);
-                    const int pc = __popcll(fresh);
-                    my_pairs += pc;
-                    my_edges += deg * pc;
+                    my_pairs += __popcll(fresh);
                 }
             }
         }
@@ -807,21 +821,22 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
                 if ((fresh >> li) & 1ull) write_lane_dist(P, li, cv, level + 1);
             }
         }
-        stage_push<true>(P, S, fresh != 0ull, (int32_t)(v < P.n ? v : 0), (int)deg, fresh, nxt,
+        stage_push<true>(P, S, fresh != 0ull, (int32_t)(v < P.n ? v : 0), 0, fresh, level, nxt,
                          nslot);
     }
-    stage_flush_all<true>(P, S, nxt, nslot);
-    // per-warp totals
+    stage_flush<true>(P, S, level, nxt, nslot);
     my_pairs = warp_incl_scan(my_pairs);
-    my_edges = warp_incl_scan(my_edges);
     if (lane == 31 && my_pairs > 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl[nslot].new_lanes),
                   (unsigned long long)my_pairs);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats->edges),
-                  (unsigned long long)my_edges);
         atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats->reached),
                   (unsigned long long)my_pairs);
     }
+    if (lane == 0 && S.edges != 0ull) {
+        atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats->edges), S.edges);
+        S.edges = 0ull;
+    }
+    __syncwarp();
 }
 
 __device__ void book_batch_level(const TraversalParams& P, int level) {

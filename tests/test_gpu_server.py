@@ -62,13 +62,18 @@ def test_mixed_queries_match_alone(setup):
 
 def test_budget_rejection_and_poll(setup):
     ctx, graphs = setup
+    # one query on a 2^18-vertex graph needs > 4 MiB (two 8-byte lane
+    # words per vertex alone), so a 1 MiB budget can never admit it
+    off, col = graphgen.kronecker(18, 4, seed=9)
+    big = bfs.Graph(ctx, off, col)
     srv = bfs.Server(ctx, 1 << 20, num_streams=1)
-    gid = srv.add_graph(graphs[2][2])
-    out = np.empty(len(graphs[2][0]) - 1, dtype=np.int32)
+    gid = srv.add_graph(big)
+    out = np.empty(len(off) - 1, dtype=np.int32)
     with pytest.raises(bfs.BfsError) as e:
         srv.submit(gid, 0, out)
     assert e.value.status == bfs.BFS_ERR_BUDGET
     srv.close()
+    big.close()
     srv = bfs.Server(ctx, 256 << 20, num_streams=1)
     gid = srv.add_graph(graphs[0][2])
     off, col, _ = graphs[0]
