@@ -198,6 +198,40 @@ bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out);
 /* Stops the server; queued queries finish with BFS_ERR_CANCELLED. */
 bfs_status bfs_server_destroy(bfs_server* s);
 
+/* ---- traversal without device allocation ---------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory at traversal time -- code that runs inside a
+ * fixed device-memory plan owned by someone else (a framework's allocator,
+ * an embedded or real-time service with its memory reserved up front), or
+ * that must not trigger the device-wide synchronisation cudaMalloc and
+ * cudaFree can imply.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * Same traversal as bfs_run, on a CSR the caller already holds on the
+ * device: row_off (int64[n+1]), col (int32[nnz], 16-byte aligned; whole
+ * 16-byte blocks are read, so the tail of the block holding the last entry
+ * must be readable, as it is for any cudaMalloc or torch buffer), dist
+ * (int32[n]) and parent (int32[n] or NULL) are device pointers on the
+ * calling thread's current device; stream as for bfs_run.  The CSR is not
+ * validated: every column index must lie in [0, n) and the offsets must not
+ * decrease (check a graph once through bfs_graph_upload if in doubt).
+ *
+ * Scratch: one fixed array of about 30 MB in the library's device code,
+ * reserved on every GPU that loads the library and held until the process
+ * exits; graphs are limited to n <= 524,288 vertices and nnz <= 33,554,432
+ * entries, larger ones fail with BFS_ERR_UNSUPPORTED.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) and the
+ * kernel's occupancy; make that first call before any stream capture.  All
+ * calls share the one array and each call clears what must start at zero,
+ * so calls whose work overlaps on the GPU (different streams, or different
+ * host threads, without ordering between them) race and give undefined
+ * results: order them on one stream.  With stats == NULL the call only
+ * enqueues the work; with a host stats pointer it waits for the stream and
+ * reports the traversal (BFS_ERR_TIMEOUT when a device-side wait expired). */
+bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col, int64_t n, int64_t nnz,
+                          int32_t root, int32_t* dist, int32_t* parent, void* stream,
+                          bfs_run_stats* stats);
+
 /* ---- diagnostics ------------------------------------------------------------ */
 const char* bfs_last_error(void);
 const char* bfs_status_string(bfs_status s);

@@ -52,6 +52,7 @@ from .api import (  # noqa: F401
     bfs_release,
     bfs_run,
     bfs_run_batch,
+    bfs_run_static,
     bfs_server_add_graph,
     bfs_server_create,
     bfs_server_destroy,

@@ -91,6 +91,7 @@ SIGNATURES = {
     "bfs_status_string": (ctypes.c_char_p, [_i32]),
     "bfs_version": (_i32, []),
     "bfs_debug_set_barrier_test": (_i32, [_vp, _i32, _i64]),
+    "bfs_run_static": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _vp, _vp, ctypes.POINTER(RunStats)]),
 }
 
 _lib = None

@@ -120,6 +120,26 @@ def bfs_run(g: int, root: int, dist, parent=None, stream=None, flags: int = 0) -
     check(_lib.lib().bfs_run(g, int(root), p_dist, p_par, _stream(stream), flags), "bfs_run")
 
 
+def bfs_run_static(row_off, col, root: int, dist, parent=None, stream=None,
+                   wait: bool = True) -> dict | None:
+    """Single-source traversal on a CSR already on the device, using the
+    library's fixed scratch (no device allocation).  Returns the traversal
+    statistics when wait is True."""
+    p_off, d_off = _buf(row_off, np.int64)
+    p_col, d_col = _buf(col, np.int32)
+    p_dist, d_dist = _buf(dist, np.int32)
+    p_par, d_par = _buf(parent, np.int32)
+    if not (d_off and d_col and d_dist and (parent is None or d_par)):
+        raise ValueError("bfs_run_static takes device buffers only")
+    n = row_off.shape[0] - 1
+    nnz = col.shape[0]
+    st = RunStats()
+    check(_lib.lib().bfs_run_static(p_off, p_col if nnz else None, n, nnz, int(root), p_dist, p_par,
+                                    _stream(stream), ctypes.byref(st) if wait else None),
+          "bfs_run_static")
+    return {f: getattr(st, f) for f, _ in RunStats._fields_} if wait else None
+
+
 def bfs_graph_sync(g: int, stream=None) -> dict:
     st = RunStats()
     check(_lib.lib().bfs_graph_sync(g, _stream(stream), ctypes.byref(st)), "bfs_graph_sync")
