@@ -24,6 +24,11 @@ cudaError_t launch_degree_bins(const int64_t* off, long long n, int t_small, int
                                unsigned long long* counts, unsigned long long* edges,
                                unsigned long long* maxdeg, int sms, cudaStream_t s);
 
+size_t relabel_scratch_bytes(long long n);
+cudaError_t relabel_graph(const int64_t* off, const int32_t* col, long long n, long long nnz,
+                          int sms, int32_t* new2old, int32_t* old2new, int64_t* new_off,
+                          int32_t* new_col, void* scratch, cudaStream_t s);
+
 static thread_local std::string t_last_error;
 
 void set_error(const std::string& msg) { t_last_error = msg; }
@@ -530,8 +535,35 @@ bfs_status bfs_graph_upload(bfs_context* ctx, const int64_t* row_off, const int3
     m->release(d_flags);
     d_flags = nullptr;
     if (!(flags & BFS_UPLOAD_NO_RELABEL)) {
-        bfs_status st = BFS_OK;
-        (void)st;  // degree-ordered renumbering is applied by launch_relabel when built in
+        // degree-ordered renumbering on the device; the uploaded copy is
+        // replaced by the renumbered one
+        int64_t* n_off = static_cast<int64_t*>(m->alloc(off_bytes));
+        int32_t* n_col = static_cast<int32_t*>(m->alloc(col_bytes));
+        g->d_new2old = static_cast<int32_t*>(m->alloc((size_t)n * 4));
+        g->d_old2new = static_cast<int32_t*>(m->alloc((size_t)n * 4));
+        void* scratch = m->alloc(relabel_scratch_bytes(n));
+        if (!n_off || !n_col || !g->d_new2old || !g->d_old2new || !scratch) {
+            m->release(n_off);
+            m->release(n_col);
+            m->release(scratch);
+            return cleanup(fail(BFS_ERR_NO_MEMORY, "device memory exhausted (renumbering)"));
+        }
+        e = relabel_graph(g->d_off, g->d_col, n, nnz, ctx->sms, g->d_new2old, g->d_old2new, n_off,
+                          n_col, scratch, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(n_col + nnz, 0, 16 * 4, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        m->release(scratch);
+        if (e != cudaSuccess) {
+            m->release(n_off);
+            m->release(n_col);
+            return cleanup(cuda_fail(e, "renumbering"));
+        }
+        m->release(g->d_off);
+        m->release(g->d_col);
+        g->d_off = n_off;
+        g->d_col = n_col;
+        g->relabelled = true;
+        g->graph_bytes += 2 * round_up((size_t)n * 4, kAlign);
     }
     bfs_status st = compute_bins(g, s);
     if (st != BFS_OK) return cleanup(st);

@@ -653,18 +653,13 @@ __device__ void seed_plain(const TraversalParams& P, Stage<false>& S) {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const bool l0 = threadIdx.x == 0;
     const int32_t root = P.old2new ? __ldg(P.old2new + P.root_caller) : P.root_caller;
-    int deg = 0;
     if (l0) {
         P.visited[root >> 5] |= 1u << (root & 31);
-        P.dist[P.root_caller] = 0;
-        if (P.parent) P.parent[P.root_caller] = P.root_caller;
-        deg = (int)(__ldg(P.off + root + 1) - __ldg(P.off + root));
         P.ctl[0].discovered = 1u;
     }
-    (void)deg;
-    // the root's distance and parent are already set; stage it with level
-    // -1 would rewrite them, so enqueue through the flush with its own values
-    stage_push<false>(P, S, l0, root, P.old2new ? root : P.root_caller, 0ull, -1, 0, 0);
+    // staged with level -1 and itself as parent: the flush writes dist 0 and
+    // parent = root, and queues the root in the bin of its degree
+    stage_push<false>(P, S, l0, root, root, 0ull, -1, 0, 0);
     stage_flush<false>(P, S, -1, 0, 0);
 }
 

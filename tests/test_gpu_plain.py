@@ -121,6 +121,32 @@ def test_kron16_all_roots_bins(ctx, kron16, name, bins):
     g.close()
 
 
+def test_relabelled_and_caller_order_uploads_agree(ctx, kron16):
+    off, col, roots = kron16
+    g1 = bfs.Graph(ctx, off, col)
+    g2 = bfs.Graph(ctx, off, col, flags=bfs.BFS_UPLOAD_NO_RELABEL)
+    assert g1.info()["relabelled"] == 1 and g2.info()["relabelled"] == 0
+    assert g1.info()["max_degree"] == g2.info()["max_degree"] == int(np.diff(off).max())
+    for r in roots[:8]:
+        d1, p1, s1 = run_gpu(g1, len(off) - 1, int(r))
+        d2, p2, s2 = run_gpu(g2, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), d1, p1, s1)
+        assert_parity(off, col, int(r), d2, p2, s2)
+    g1.close()
+    g2.close()
+
+
+@pytest.mark.parametrize("name,bins", BIN_SETTINGS[1:4], ids=[b[0] for b in BIN_SETTINGS[1:4]])
+def test_caller_order_bins(ctx, kron16, name, bins):
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col, flags=bfs.BFS_UPLOAD_NO_RELABEL)
+    g.set_bins(*bins)
+    for r in roots[:6]:
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+    g.close()
+
+
 def test_kron16_host_loop_and_host_outputs(ctx, kron16):
     off, col, roots = kron16
     g = bfs.Graph(ctx, off, col)
