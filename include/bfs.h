@@ -100,17 +100,18 @@ typedef struct bfs_graph_info {
     int64_t max_degree;
     int32_t t_small;        /* degree bins: deg < t_small -> warp-gather bin */
     int32_t t_large;        /* deg >= t_large -> CTA bin, otherwise warp bin */
-    int32_t chunk_warp;     /* edges per warp work item (warp bin) */
-    int32_t chunk_cta;      /* edges per CTA work item (CTA bin) */
+    int32_t chunk_warp;     /* edges per base chunk of the warp bin (a work item
+                               takes 1-16 base chunks, more on larger levels) */
+    int32_t chunk_cta;      /* edges per base chunk of the CTA bin (1-32 per item) */
     int32_t relabelled;     /* 1 when the device copy is degree-ordered */
     int32_t grid_blocks;    /* persistent grid size used by the device loop */
     size_t device_bytes;    /* device memory held by the graph and its buffers */
 } bfs_graph_info;
 bfs_status bfs_graph_get_info(const bfs_graph* g, bfs_graph_info* out);
 
-/* Degree-bin thresholds and work-item sizes (the autotuner's knobs).
+/* Degree-bin thresholds and base chunk sizes (the autotuner's knobs).
  * t_small >= 1, t_large > t_small, chunk_warp a multiple of 128,
- * chunk_cta a multiple of 1024.  Reallocates the per-traversal buffers;
+ * chunk_cta a multiple of 1024.  Defaults 32, 4096, 512, 2048.  Reallocates the per-traversal buffers;
  * must not be called while a traversal on g is in flight. */
 bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
                               int32_t chunk_warp, int32_t chunk_cta);
@@ -123,10 +124,35 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *                            in ns (default 2e9); expiry ends the traversal
  *                            with BFS_ERR_TIMEOUT.
  *   BFS_OPT_CTAS_PER_SM      2 or 3: resident CTAs per SM of the traversal
- *                            kernels (register cap 128 or 80; default 2). */
+ *                            kernels (register cap 128 or 80; default 3).
+ *   BFS_OPT_HOT_WORDS        visited-bitmap words (multiple of 4, <= 40960)
+ *                            each CTA copies to shared memory at the start of
+ *                            a large level; probes of vertices below 32x that
+ *                            index that were visited before the level end
+ *                            there.  Default 0 (off).
+ *   BFS_OPT_HOT_MIN_EDGES    a level is large when its frontier holds at least
+ *                            this many adjacency entries (default 2^20).
+ *   BFS_OPT_DIRECTION        0: every level top-down (Algorithm 1; default).
+ *                            1: direction-optimizing -- a level runs bottom-up
+ *                            (every unvisited vertex looks for a neighbour in
+ *                            the frontier bitmap) when the frontier's edges
+ *                            times alpha exceed the unvisited vertices' edges,
+ *                            and returns to top-down when the frontier holds
+ *                            fewer than n / beta vertices.  2: bottom-up on
+ *                            every level (for testing).  Distances are the
+ *                            same in every mode.  Modes 1 and 2 need a
+ *                            symmetric graph (bottom-up follows a vertex's own
+ *                            adjacency); the upload tests symmetry and other
+ *                            graphs refuse them with BFS_ERR_UNSUPPORTED.
+ *   BFS_OPT_DO_ALPHA, BFS_OPT_DO_BETA   the two thresholds (default 15, 18). */
 #define BFS_OPT_WARP_AGGREGATE  1
 #define BFS_OPT_TIMEOUT_NS      2
 #define BFS_OPT_CTAS_PER_SM     3
+#define BFS_OPT_HOT_WORDS       4
+#define BFS_OPT_HOT_MIN_EDGES   5
+#define BFS_OPT_DIRECTION       6
+#define BFS_OPT_DO_ALPHA        7
+#define BFS_OPT_DO_BETA         8
 bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value);
 
 /* ---- single-source traversal ----------------------------------------------
@@ -143,8 +169,11 @@ bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* dist, int32_t* parent, v
 typedef struct bfs_run_stats {
     int64_t levels;         /* number of non-empty frontiers (max dist + 1) */
     int64_t reached;        /* vertices with dist >= 0 */
-    int64_t edges_scanned;  /* adjacency entries expanded (m_c, TEPS numerator) */
+    int64_t edges_scanned;  /* m_c: sum of the out-degrees of the reached vertices --
+                               the entries a top-down traversal expands and the
+                               TEPS numerator in every direction mode */
     int32_t status;         /* device-side status of the last traversal */
+    int32_t bottom_up_levels; /* levels run bottom-up (BFS_OPT_DIRECTION) */
 } bfs_run_stats;
 /* Waits for `stream`, then reports the last traversal run on g. */
 bfs_status bfs_graph_sync(bfs_graph* g, void* stream, bfs_run_stats* stats);

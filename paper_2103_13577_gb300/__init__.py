@@ -24,6 +24,11 @@ from ._lib import (  # noqa: F401
     BFS_ERR_UNSUPPORTED,
     BFS_HOST_LOOP,
     BFS_OPT_CTAS_PER_SM,
+    BFS_OPT_DIRECTION,
+    BFS_OPT_DO_ALPHA,
+    BFS_OPT_DO_BETA,
+    BFS_OPT_HOT_MIN_EDGES,
+    BFS_OPT_HOT_WORDS,
     BFS_OPT_TIMEOUT_NS,
     BFS_OPT_WARP_AGGREGATE,
     BFS_OK,

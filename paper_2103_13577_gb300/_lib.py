@@ -32,6 +32,11 @@ BFS_HOST_LOOP = 0x4
 BFS_OPT_WARP_AGGREGATE = 1
 BFS_OPT_TIMEOUT_NS = 2
 BFS_OPT_CTAS_PER_SM = 3
+BFS_OPT_HOT_WORDS = 4
+BFS_OPT_HOT_MIN_EDGES = 5
+BFS_OPT_DIRECTION = 6
+BFS_OPT_DO_ALPHA = 7
+BFS_OPT_DO_BETA = 8
 
 
 class BfsError(RuntimeError):
@@ -50,7 +55,8 @@ class GraphInfo(ctypes.Structure):
 
 class RunStats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int64), ("reached", ctypes.c_int64),
-                ("edges_scanned", ctypes.c_int64), ("status", ctypes.c_int32)]
+                ("edges_scanned", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("bottom_up_levels", ctypes.c_int32)]
 
 
 class ServerStats(ctypes.Structure):

@@ -20,6 +20,8 @@ const void* batch_persistent_fn(int mb);
 const void* batch_step_fn(int mb);
 cudaError_t launch_csr_check(const int64_t* off, const int32_t* col, long long n, long long nnz,
                              int* flags, int sms, cudaStream_t s);
+cudaError_t launch_symmetry_hash(const int64_t* off, const int32_t* col, long long n,
+                                 unsigned long long* sums, int sms, cudaStream_t s);
 cudaError_t launch_degree_bins(const int64_t* off, long long n, int t_small, int t_large,
                                unsigned long long* counts, unsigned long long* edges,
                                unsigned long long* maxdeg, int sms, cudaStream_t s);
@@ -130,7 +132,7 @@ static size_t control_bytes() {
 
 size_t workspace_bytes(const bfs_graph* g, bool batched, int /*nlanes*/) {
     size_t b = control_bytes();
-    if (!batched) b += round_up(((g->n + 31) / 32 + 8) * 4, kAlign);
+    if (!batched) b += 4 * round_up(((g->n + 31) / 32 + 8) * 4, kAlign);  // visited + 3 frontier maps
     for (int bin = 0; bin < kBins; ++bin) {
         const size_t cap = g->bin_count[bin] + 1;
         const int64_t C = bin == 1 ? g->chunk_warp : g->chunk_cta;
@@ -153,6 +155,7 @@ void free_workspace(bfs_graph* g, Workspace* ws) {
         return;
     }
     m->release(ws->visited);
+    for (int f = 0; f < 3; ++f) m->release(ws->fb[f]);
     for (int p = 0; p < 2; ++p)
         for (int b = 0; b < kBins; ++b) {
             m->release(ws->q[p][b].v);
@@ -185,7 +188,10 @@ Workspace* make_workspace(bfs_graph* g, DeviceAllocator* m, bool batched, cudaSt
         ws->bytes += round_up(std::max<size_t>(bytes, 1), kAlign);
         return p;
     };
-    if (!batched) ws->visited = static_cast<uint32_t*>(get(((g->n + 31) / 32 + 8) * 4));
+    if (!batched) {
+        ws->visited = static_cast<uint32_t*>(get(((g->n + 31) / 32 + 8) * 4));
+        for (int f = 0; f < 3; ++f) ws->fb[f] = static_cast<uint32_t*>(get(((g->n + 31) / 32 + 8) * 4));
+    }
     for (int p = 0; p < 2; ++p)
         for (int b = 0; b < kBins; ++b) {
             BinQueue& Q = ws->q[p][b];
@@ -245,15 +251,42 @@ static void fill_params(bfs_graph* g, Workspace* ws, TraversalParams& P) {
     P.timeout_ns = g->timeout_ns;
     P.debug_stall = g->debug_stall;
     P.use_match_any = g->use_match_any;
+    P.hot_words = g->hot_words;
+    P.hot_min_edges = g->hot_min_edges;
+    for (int f = 0; f < 3; ++f) P.fb[f] = ws->fb[f];
+    P.nnz = g->nnz;
+    P.bu_limit = g->relabelled ? g->n_nonzero : g->n;
+    P.dir_mode = g->dir_mode;
+    P.do_alpha = g->do_alpha;
+    P.do_beta = g->do_beta;
+    P.dir_override = -1;
 }
 
-static bfs_status grid_size(bfs_graph* g, const void* fn, int32_t* out) {
+static size_t plain_smem(const bfs_graph* g) { return (size_t)g->hot_words * 4; }
+
+static bfs_status grid_size(bfs_graph* g, const void* fn, int32_t* out, size_t smem = 0) {
     int nb = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBlock, 0);
+    // the limit is a property of the kernel, shared by every graph: only raise it
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes < smem)
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "dynamic shared memory size");
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, kBlock, smem);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
     if (nb < 1) return fail(BFS_ERR_CUDA, "traversal kernel cannot be resident");
     *out = nb * g->ctx->sms;
     return BFS_OK;
+}
+
+// Plain-kernel grids for the graph's shared-memory setting (both the
+// persistent kernel and the host-loop step kernel take the same size).
+static bfs_status set_plain_grids(bfs_graph* g) {
+    const size_t smem = plain_smem(g);
+    int32_t grid2 = 0;
+    bfs_status st = grid_size(g, plain_step_fn(g->min_blocks), &grid2, smem);
+    if (st != BFS_OK) return st;
+    return grid_size(g, plain_persistent_fn(g->min_blocks), &g->grid_plain, smem);
 }
 
 static bfs_status dev_status(int s) {
@@ -265,17 +298,18 @@ static bfs_status dev_status(int s) {
     }
 }
 
-static bfs_status launch_coop(const void* fn, int grid, TraversalParams& P, cudaStream_t s) {
+static bfs_status launch_coop(const void* fn, int grid, TraversalParams& P, cudaStream_t s,
+                              size_t smem = 0) {
     void* args[] = {&P};
-    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+    cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "cooperative launch");
     return BFS_OK;
 }
 
 static bfs_status launch_plain_kernel(const void* fn, int grid, TraversalParams& P,
-                                      cudaStream_t s) {
+                                      cudaStream_t s, size_t smem = 0) {
     void* args[] = {&P};
-    cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, 0, s);
+    cudaError_t e = cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, smem, s);
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
     return BFS_OK;
 }
@@ -300,22 +334,39 @@ static bfs_status run_plain(bfs_graph* g, Workspace* ws, int32_t root, int32_t* 
     P.dist = dist;
     P.parent = parent;
     P.root_caller = root;
-    if (!(flags & BFS_HOST_LOOP)) return launch_coop(plain_persistent_fn(g->min_blocks), g->grid_plain, P, s);
+    const size_t smem = plain_smem(g);
+    if (!(flags & BFS_HOST_LOOP))
+        return launch_coop(plain_persistent_fn(g->min_blocks), g->grid_plain, P, s, smem);
     // host-driven level loop: init, seed, then one launch per level
     bfs_status st;
+    const void* fn = plain_step_fn(g->min_blocks);
     P.phase = 0;
-    if ((st = launch_plain_kernel(plain_step_fn(g->min_blocks), g->grid_plain, P, s)) != BFS_OK) return st;
+    if ((st = launch_plain_kernel(fn, g->grid_plain, P, s, smem)) != BFS_OK) return st;
     P.phase = 1;
-    if ((st = launch_plain_kernel(plain_step_fn(g->min_blocks), 1, P, s)) != BFS_OK) return st;
+    if ((st = launch_plain_kernel(fn, 1, P, s, smem)) != BFS_OK) return st;
     P.phase = 2;
+    // the host takes the same direction decisions as the device loop
+    LevelCtl c;
+    if ((st = read_ctl(ws, 0, &c, s)) != BFS_OK) return st;
+    long long seen_edges = 0;
+    bool prev_bu = false;
     for (int level = 0;; ++level) {
+        long long nf = 0, mf = 0;
+        for (int b = 0; b < kBins; ++b) {
+            nf += (long long)(c.packed[b] >> kCountShift);
+            mf += (long long)(c.packed[b] & kEdgeMask);
+        }
+        seen_edges += mf;
+        const int dir = choose_direction(g->dir_mode, prev_bu, mf, g->nnz - seen_edges, nf, g->n,
+                                         g->do_alpha, g->do_beta);
+        prev_bu = dir == 2;
         P.level = level;
-        if ((st = launch_plain_kernel(plain_step_fn(g->min_blocks), g->grid_plain, P, s)) != BFS_OK) return st;
-        LevelCtl c;
+        P.dir_override = dir;
+        if ((st = launch_plain_kernel(fn, g->grid_plain, P, s, smem)) != BFS_OK) return st;
         if ((st = read_ctl(ws, (level + 1) % 3, &c, s)) != BFS_OK) return st;
         if (ctl_empty(c)) {
             P.level = level + 1;  // books the last level's discoveries
-            return launch_plain_kernel(plain_step_fn(g->min_blocks), 1, P, s);
+            return launch_plain_kernel(fn, 1, P, s, smem);
         }
     }
 }
@@ -369,6 +420,7 @@ static bfs_status finish(Workspace* ws, cudaStream_t s, bfs_run_stats* out) {
         out->reached = h.reached;
         out->edges_scanned = h.edges;
         out->status = h.status;
+        out->bottom_up_levels = h.bu_levels;
     }
     return dev_status(h.status);
 }
@@ -474,6 +526,7 @@ static bfs_status compute_bins(bfs_graph* g, cudaStream_t s) {
         g->bin_edges[b] = h[3 + b];
     }
     g->max_degree = (int64_t)h[6];
+    g->n_nonzero = (int64_t)(h[0] + h[1] + h[2]);
     return BFS_OK;
 }
 
@@ -532,6 +585,17 @@ bfs_status bfs_graph_upload(bfs_context* ctx, const int64_t* row_off, const int3
         return cleanup(fail(BFS_ERR_INVALID_GRAPH, "row_off[0] must be 0 and row_off[n] must be nnz"));
     if (h_flags & 2) return cleanup(fail(BFS_ERR_INVALID_GRAPH, "row offsets decrease"));
     if (h_flags & 1) return cleanup(fail(BFS_ERR_INVALID_GRAPH, "column index out of range"));
+    {
+        // symmetric graphs (each edge stored both ways) may run bottom-up levels
+        unsigned long long h[2] = {0, 0};
+        unsigned long long* d_sums = reinterpret_cast<unsigned long long*>(d_flags);
+        e = cudaMemsetAsync(d_sums, 0, 16, s);
+        if (e == cudaSuccess) e = launch_symmetry_hash(g->d_off, g->d_col, n, d_sums, ctx->sms, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_sums, 16, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cleanup(cuda_fail(e, "symmetry test"));
+        g->symmetric = h[0] == h[1];
+    }
     m->release(d_flags);
     d_flags = nullptr;
     if (!(flags & BFS_UPLOAD_NO_RELABEL)) {
@@ -567,7 +631,11 @@ bfs_status bfs_graph_upload(bfs_context* ctx, const int64_t* row_off, const int3
     }
     bfs_status st = compute_bins(g, s);
     if (st != BFS_OK) return cleanup(st);
-    if ((st = grid_size(g, plain_persistent_fn(g->min_blocks), &g->grid_plain)) != BFS_OK) return cleanup(st);
+    // the shared-memory copy of the hot bitmap prefix is off by default: on
+    // GB300 the degree-ordered bitmap's hot words already hit in L1, and the
+    // shared memory it takes shrinks that L1 (measured slower)
+    g->hot_words = 0;
+    if ((st = set_plain_grids(g)) != BFS_OK) return cleanup(st);
     if ((st = grid_size(g, batch_persistent_fn(g->min_blocks), &g->grid_batch)) != BFS_OK) return cleanup(st);
     Workspace* ws = nullptr;
     if ((st = ensure_workspace(g, false, s, &ws)) != BFS_OK) return cleanup(st);
@@ -730,10 +798,37 @@ bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value) {
     case BFS_OPT_CTAS_PER_SM: {
         if (value != 2 && value != 3) return fail(BFS_ERR_INVALID_ARG, "value must be 2 or 3");
         g->min_blocks = (int32_t)value;
-        bfs_status st = grid_size(g, plain_persistent_fn(g->min_blocks), &g->grid_plain);
+        bfs_status st = set_plain_grids(g);
         if (st == BFS_OK) st = grid_size(g, batch_persistent_fn(g->min_blocks), &g->grid_batch);
         return st;
     }
+    case BFS_OPT_HOT_WORDS: {
+        if (value < 0 || value > 40960 || value % 4) return fail(BFS_ERR_INVALID_ARG, "hot words must be a multiple of 4 in [0, 40960]");
+        const int32_t old = g->hot_words;
+        g->hot_words = (int32_t)value;
+        bfs_status st = set_plain_grids(g);
+        if (st != BFS_OK) {
+            g->hot_words = old;
+            set_plain_grids(g);
+        }
+        return st;
+    }
+    case BFS_OPT_HOT_MIN_EDGES:
+        if (value < 0) return fail(BFS_ERR_INVALID_ARG, "must be >= 0");
+        g->hot_min_edges = value;
+        return BFS_OK;
+    case BFS_OPT_DIRECTION:
+        if (value < 0 || value > 2) return fail(BFS_ERR_INVALID_ARG, "direction must be 0, 1 or 2");
+        if (value != 0 && !g->symmetric)
+            return fail(BFS_ERR_UNSUPPORTED,
+                        "bottom-up levels need a symmetric graph (every edge stored both ways)");
+        g->dir_mode = (int32_t)value;
+        return BFS_OK;
+    case BFS_OPT_DO_ALPHA:
+    case BFS_OPT_DO_BETA:
+        if (value < 1 || value > (1 << 20)) return fail(BFS_ERR_INVALID_ARG, "must be in [1, 2^20]");
+        (option == BFS_OPT_DO_ALPHA ? g->do_alpha : g->do_beta) = (int32_t)value;
+        return BFS_OK;
     default: return fail(BFS_ERR_INVALID_ARG, "unknown option");
     }
 }

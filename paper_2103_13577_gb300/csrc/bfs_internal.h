@@ -41,7 +41,8 @@ struct DevStats {
     int status;       // sticky result of the launch (read by the host)
     int max_level;
     int abort;        // set with status; tells waiting CTAs to leave; cleared at kernel exit
-    int pad[3];
+    int bu_levels;    // levels run bottom-up
+    int pad[2];
 };
 
 // Frontier queue of one bin (one of two ping-pong copies).
@@ -88,6 +89,29 @@ struct TraversalParams {
     long long timeout_ns;
     int32_t debug_stall;
     int32_t use_match_any;    // warp-aggregated atomicOr on the visited bitmap
+    int32_t hot_words;        // visited words copied to shared memory on large levels (0: off)
+    long long hot_min_edges;  // a level is large when its frontier has this many edges
+    // frontier bitmaps and the bottom-up step (plain traversal)
+    uint32_t* fb[3];          // frontier of level L in fb[L % 3]; nullptr: not kept
+    long long nnz;
+    long long bu_limit;       // bottom-up scans vertices [0, bu_limit)
+    int32_t dir_mode;         // 0 top-down, 1 direction-optimizing, 2 bottom-up on every level
+    int32_t do_alpha;         // top-down -> bottom-up when frontier edges * alpha > unvisited edges
+    int32_t do_beta;          // bottom-up -> top-down when frontier vertices * beta < n
+    int32_t dir_override;     // host-loop launches: direction chosen by the host (-1: device)
 };
+
+// Direction of level L (Beamer, Asanovic, Patterson, "Direction-optimizing
+// breadth-first search", SC 2012): 0 = top-down, 2 = bottom-up.  m_f: edges
+// of the frontier, m_u: edges of the vertices not yet visited, n_f:
+// frontier vertices.
+__host__ __device__ inline int choose_direction(int mode, bool prev_bu, long long m_f,
+                                                long long m_u, long long n_f, long long n,
+                                                int alpha, int beta) {
+    if (mode == 0) return 0;
+    if (mode == 2) return 2;
+    if (!prev_bu) return (m_f * (long long)alpha > m_u) ? 2 : 0;
+    return (n_f * (long long)beta < n) ? 0 : 2;
+}
 
 }  // namespace bfs

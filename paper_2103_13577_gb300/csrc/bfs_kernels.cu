@@ -148,6 +148,8 @@ struct Stage {
     unsigned long long mask[kBatch ? kStageCap : 1];   // batched: new lanes of u
     int cnt;
     unsigned long long edges;                          // batched: sum deg * lanes
+    const uint32_t* hot;                               // plain: shared copy of visited[0, hot_bits)
+    int hot_bits;                                      // 0 when the copy is off for this level
 };
 
 // Warp-collective flush of the staged entries into the next frontier.
@@ -185,6 +187,7 @@ __device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>
             const int32_t cv = P.new2old ? __ldg(P.new2old + vv) : vv;
             P.dist[cu] = level + 1;
             if (P.parent) P.parent[cu] = cv;
+            if (P.fb[0]) atomicOr(P.fb[(level + 1) % 3] + (u[h] >> 5), 1u << (u[h] & 31));
         }
     }
 #pragma unroll
@@ -268,6 +271,8 @@ __device__ __forceinline__ void stage_init(Stage<kBatch>& S) {
     if (lane_id() == 0) {
         S.cnt = 0;
         S.edges = 0ull;
+        S.hot = nullptr;
+        S.hot_bits = 0;
     }
     __syncwarp();
 }
@@ -281,6 +286,17 @@ __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<fa
                                               unsigned okm, const int32_t (&u)[K],
                                               const int32_t (&v)[K], int level, int nxt,
                                               int nslot, int& my_disc) {
+    // pass 1 (shared memory only): drop edges whose target was visited before
+    // the level and lies in the hot prefix copied at level start
+    const int hot_bits = S.hot_bits;
+    if (hot_bits > 0) {
+        const uint32_t* hot = S.hot;
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (((okm >> j) & 1u) && u[j] < hot_bits && ((hot[u[j] >> 5] >> (u[j] & 31)) & 1u))
+                okm &= ~(1u << j);
+    }
+    // pass 2: independent global probes for the rest
     uint32_t w[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) w[j] = ((okm >> j) & 1u) ? P.visited[u[j] >> 5] : 0xffffffffu;
@@ -455,43 +471,84 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
     }
 }
 
-// Bin 1: one warp per chunk of chunk_warp edges; inside it, one vertex
-// segment at a time, the whole warp reading it with 128-bit loads.
+// Bin 1: one warp per chunk of chunk_warp edges.  The chunk's vertex
+// segments (up to 32 at a time) are cut into 16-byte units (4 columns, the
+// first rounded down to a 16-byte boundary) laid end to end by a scan; each
+// round a lane takes two units, finds their segments by a shuffle binary
+// search, and reads each with one 128-bit load -- short and long segments
+// alike keep every lane busy.
 template <bool kBatch>
 __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
-                                  long long chunk, long long cnt, long long E, int level, int nxt,
-                                  int nslot, int& my_disc) {
+                                  long long item, int k, long long cnt, long long E, int level,
+                                  int nxt, int nslot, int& my_disc) {
     const BinQueue& Q = P.q[cur][1];
     const unsigned lane = lane_id();
-    const long long cs = chunk * (long long)P.chunk_warp;
-    const long long ce = min(cs + (long long)P.chunk_warp, E);
-    long long i = __ldcg(Q.chunk + chunk);
+    const long long cs = item * k * (long long)P.chunk_warp;
+    const long long ce = min(cs + k * (long long)P.chunk_warp, E);
+    long long i = __ldcg(Q.chunk + item * k);
     for (;;) {
         const long long ij = i + lane;
         long long eo = 0x7fffffffffffffffll;
         if (ij < cnt) eo = __ldcg(Q.eoff + ij);
         const bool ok = eo < ce;
         int32_t v = 0;
-        long long base = 0, end = 0;
+        long long a = 0, b = 0;
         uint64_t mask = 0ull;
         if (ok) {
             v = __ldcg(Q.v + ij);
-            base = __ldg(P.off + v);
-            end = __ldg(P.off + v + 1);
+            const long long base = __ldg(P.off + v), end = __ldg(P.off + v + 1);
+            const long long lo = max(eo, cs), hi = min(eo + (end - base), ce);
+            a = base + (lo - eo);
+            b = base + (hi - eo);
             if (kBatch) mask = __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij);
         }
-        const int nent = __popc(__ballot_sync(FULL_MASK, ok));
-        for (int k = 0; k < nent; ++k) {
-            const long long eok = __shfl_sync(FULL_MASK, eo, k);
-            const long long bk = __shfl_sync(FULL_MASK, base, k);
-            const long long ek = __shfl_sync(FULL_MASK, end, k);
-            const int32_t vk = __shfl_sync(FULL_MASK, v, k);
-            const uint64_t mk = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, k) : 0ull;
-            const long long lo = max(eok, cs), hi = min(eok + (ek - bk), ce);
-            expand_segment<kBatch>(P, S, bk + (lo - eok), bk + (hi - eok), vk, mk, level, nxt,
-                                   nslot, 0, 256, my_disc);
+        const unsigned okb = __ballot_sync(FULL_MASK, ok);
+        const long long a4 = a & ~3ll;
+        const int rlo = (int)(a - a4), rhi = (int)(b - a4);  // valid columns, relative to a4
+        const int units = ok ? (rhi + 3) >> 2 : 0;
+        const int incl = warp_incl_scan(units);
+        const int excl = incl - units;
+        const int total = __shfl_sync(FULL_MASK, incl, 31);
+        for (int q0 = 0; q0 < total; q0 += 64) {
+            unsigned okm = 0u;
+            int32_t u[8], vv[8];
+            uint64_t mm[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = q0 + 32 * h + (int)lane;
+                int o = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int c = o + st;
+                    if (__shfl_sync(FULL_MASK, excl, c & 31) <= q) o = c;
+                }
+                const long long a4o = __shfl_sync(FULL_MASK, a4, o);
+                const int lo_o = __shfl_sync(FULL_MASK, rlo, o);
+                const int hi_o = __shfl_sync(FULL_MASK, rhi, o);
+                const int xo = __shfl_sync(FULL_MASK, excl, o);
+                const int32_t vo = __shfl_sync(FULL_MASK, v, o);
+                const uint64_t mo = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, o) : 0ull;
+                const int r = 4 * (q - xo);
+                int4 x = make_int4(0, 0, 0, 0);
+                if (q < total) {
+                    x = __ldcs(reinterpret_cast<const int4*>(P.col + a4o + r));
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (r + c >= lo_o && r + c < hi_o) okm |= 1u << (4 * h + c);
+                }
+                u[4 * h + 0] = x.x;
+                u[4 * h + 1] = x.y;
+                u[4 * h + 2] = x.z;
+                u[4 * h + 3] = x.w;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    vv[4 * h + c] = vo;
+                    mm[4 * h + c] = mo;
+                }
+            }
+            visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
         }
-        if (nent < 32) break;
+        if (__popc(okb) < 32) break;
         i += 32;
     }
 }
@@ -500,16 +557,16 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
 // chunks, hence many CTAs); the CTA's warps interleave over each segment.
 template <bool kBatch>
 __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
-                                 long long chunk, long long cnt, long long E, int level, int nxt,
-                                 int nslot, int& my_disc) {
+                                 long long item, int k, long long cnt, long long E, int level,
+                                 int nxt, int nslot, int& my_disc) {
     __shared__ long long s_eo[kBlock], s_base[kBlock], s_end[kBlock];
     __shared__ int32_t s_v[kBlock];
     __shared__ unsigned long long s_mask[kBatch ? kBlock : 1];
     const BinQueue& Q = P.q[cur][2];
     const int warp = threadIdx.x >> 5;
-    const long long cs = chunk * (long long)P.chunk_cta;
-    const long long ce = min(cs + (long long)P.chunk_cta, E);
-    long long i = __ldcg(Q.chunk + chunk);
+    const long long cs = item * k * (long long)P.chunk_cta;
+    const long long ce = min(cs + k * (long long)P.chunk_cta, E);
+    long long i = __ldcg(Q.chunk + item * k);
     for (;;) {
         const long long ij = i + threadIdx.x;
         long long eo = 0x7fffffffffffffffll;
@@ -541,9 +598,16 @@ __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int
 
 struct LevelShape {
     long long cnt[kBins], edges[kBins];
-    long long n_cta, chunks_warp, groups_small;
+    long long n_cta, chunks_warp, groups_small;  // work items (CTA chunks, warp chunks, groups)
+    int k_cta, k_warp;                           // base chunks per work item
     unsigned discovered;
 };
+
+__device__ __forceinline__ int pow2_floor_clamped(long long x, int kmax) {
+    if (x <= 1) return 1;
+    const int p = 63 - __clzll((unsigned long long)x);
+    return p >= 31 ? kmax : min(1 << p, kmax);
+}
 
 // Shape of level `level` (frontier in slot level % 3, queues level & 1).
 // Counts are clamped to the queue capacities so that a recorded overflow
@@ -558,9 +622,17 @@ __device__ __forceinline__ LevelShape read_level(const TraversalParams& P, int l
         s.edges[b] = (long long)(p & kEdgeMask);
     }
     s.discovered = __ldcg(&P.ctl[slot].discovered);
-    s.n_cta = min((s.edges[2] + P.chunk_cta - 1) / P.chunk_cta, (long long)P.q[cur][2].chunk_cap);
-    s.chunks_warp =
+    // base chunks (the granularity of the chunk tables), then work items of k
+    // base chunks: small levels keep k = 1 so that every CTA / warp gets work,
+    // large levels aim at ~4 items per CTA (or warp) to bound per-item costs
+    const long long base_cta =
+        min((s.edges[2] + P.chunk_cta - 1) / P.chunk_cta, (long long)P.q[cur][2].chunk_cap);
+    const long long base_warp =
         min((s.edges[1] + P.chunk_warp - 1) / P.chunk_warp, (long long)P.q[cur][1].chunk_cap);
+    s.k_cta = pow2_floor_clamped(base_cta / (4ll * gridDim.x), 32);
+    s.k_warp = pow2_floor_clamped(base_warp / (4ll * gridDim.x * kWarps), 16);
+    s.n_cta = (base_cta + s.k_cta - 1) / s.k_cta;
+    s.chunks_warp = (base_warp + s.k_warp - 1) / s.k_warp;
     s.groups_small = (s.cnt[0] + 31) / 32;
     return s;
 }
@@ -571,17 +643,60 @@ __device__ __forceinline__ LevelShape read_level(const TraversalParams& P, int l
 // round robin over all warps of the grid, with no atomics or CTA barriers.
 // Each warp flushes its staged discoveries at the end; the CTA adds its
 // discovered-vertex count with one atomic.
+// Bottom-up level (Section "Top Down Vs. Bottom Up"; the paper notes its
+// exchange works with either direction): every vertex not yet visited looks
+// for a neighbour in the current frontier bitmap and stops at the first.
+// A warp owns one 32-vertex visited word at a time, so claims need no
+// atomics.  Found vertices go through the same stage as top-down winners
+// (distance level + 1, parent = the frontier neighbour, next frontier).
+__device__ void bottom_up_level(const TraversalParams& P, Stage<false>& S, int level, int nxt,
+                                int nslot, int& my_disc) {
+    const uint32_t* F = P.fb[level % 3];
+    const unsigned lane = lane_id();
+    const long long words = (P.bu_limit + 31) / 32;
+    const long long nwarps = (long long)gridDim.x * kWarps;
+    for (long long w = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); w < words; w += nwarps) {
+        const uint32_t vis = __ldcg(P.visited + w);
+        const long long v = w * 32 + lane;
+        const bool unv = v < P.bu_limit && !((vis >> lane) & 1u);
+        if (__ballot_sync(FULL_MASK, unv) == 0u) continue;
+        bool found = false;
+        int32_t par = 0;
+        if (unv) {
+            long long k = __ldg(P.off + v);
+            const long long e = __ldg(P.off + v + 1);
+            for (; k + 4 <= e && !found; k += 4) {
+                const int32_t u0 = __ldg(P.col + k), u1 = __ldg(P.col + k + 1);
+                const int32_t u2 = __ldg(P.col + k + 2), u3 = __ldg(P.col + k + 3);
+                const uint32_t f0 = F[u0 >> 5], f1 = F[u1 >> 5], f2 = F[u2 >> 5], f3 = F[u3 >> 5];
+                if ((f0 >> (u0 & 31)) & 1u) { found = true; par = u0; }
+                else if ((f1 >> (u1 & 31)) & 1u) { found = true; par = u1; }
+                else if ((f2 >> (u2 & 31)) & 1u) { found = true; par = u2; }
+                else if ((f3 >> (u3 & 31)) & 1u) { found = true; par = u3; }
+            }
+            for (; k < e && !found; ++k) {
+                const int32_t u0 = __ldg(P.col + k);
+                if ((F[u0 >> 5] >> (u0 & 31)) & 1u) { found = true; par = u0; }
+            }
+        }
+        const unsigned fm = __ballot_sync(FULL_MASK, found);
+        if (fm == 0u) continue;
+        if (lane == 0) P.visited[w] = vis | fm;
+        my_disc += found ? 1 : 0;
+        stage_push<false>(P, S, found, (int32_t)v, par, 0ull, level, nxt, nslot);
+    }
+}
+
+// Top-down work of one level: CTA chunks of bin 2 pulled from a counter
+// (heavy vertices spread over whichever CTAs are free), then warp items
+// (bin 1 chunks, bin 0 groups) dealt round robin over all warps of the grid.
 template <bool kBatch>
-__device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
-                             int level) {
+__device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
+                                int level, int& my_disc) {
     __shared__ long long s_item;
-    __shared__ int s_disc;
     const int slot = level % 3, nslot = (level + 1) % 3;
     const int cur = level & 1, nxt = cur ^ 1;
     const int warp = threadIdx.x >> 5;
-    int my_disc = 0;
-    if (threadIdx.x == 0) s_disc = 0;
-    __syncthreads();
     if (L.n_cta > 0) {
         for (;;) {
             if (threadIdx.x == 0) s_item = (long long)atomicAdd(&P.ctl[slot].work, 1u);
@@ -589,8 +704,8 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
             const long long item = s_item;
             __syncthreads();
             if (item >= L.n_cta) break;
-            expand_cta_chunk<kBatch>(P, S, cur, item, L.cnt[2], L.edges[2], level, nxt, nslot,
-                                     my_disc);
+            expand_cta_chunk<kBatch>(P, S, cur, item, L.k_cta, L.cnt[2], L.edges[2], level, nxt,
+                                     nslot, my_disc);
         }
     }
     const long long nwarps = (long long)gridDim.x * kWarps;
@@ -598,12 +713,50 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
     const long long witems = L.chunks_warp + L.groups_small;
     for (long long it = gw; it < witems; it += nwarps) {
         if (it < L.chunks_warp)
-            expand_warp_chunk<kBatch>(P, S, cur, it, L.cnt[1], L.edges[1], level, nxt, nslot,
-                                      my_disc);
+            expand_warp_chunk<kBatch>(P, S, cur, it, L.k_warp, L.cnt[1], L.edges[1], level, nxt,
+                                      nslot, my_disc);
         else
             expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt, nslot,
                                        my_disc);
     }
+}
+
+template <bool kBatch>
+__device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
+                             int level, uint32_t* s_hot, int dir = 0) {
+    __shared__ int s_disc;
+    const int nslot = (level + 1) % 3;
+    const int nxt = (level & 1) ^ 1;
+    int my_disc = 0;
+    if (threadIdx.x == 0) s_disc = 0;
+    if (!kBatch) {
+        // large levels: copy the hot prefix of the visited bitmap (after the
+        // degree-ordered renumbering, the highest-degree vertices) into
+        // shared memory; most probes of a dense level end there
+        const long long ledges = L.edges[0] + L.edges[1] + L.edges[2];
+        const int words = (P.hot_words > 0 && ledges >= P.hot_min_edges)
+                              ? (int)min((long long)P.hot_words, (long long)((P.n + 31) / 32)) : 0;
+        if (words > 0) {
+            const int w4 = words / 4;
+            const uint4* src = reinterpret_cast<const uint4*>(P.visited);
+            uint4* dst = reinterpret_cast<uint4*>(s_hot);
+            for (int i = threadIdx.x; i < w4; i += kBlock) dst[i] = __ldcg(src + i);
+            for (int i = w4 * 4 + threadIdx.x; i < words; i += kBlock) s_hot[i] = __ldcg(P.visited + i);
+        }
+        if (lane_id() == 0) {
+            S.hot = s_hot;
+            S.hot_bits = words * 32;
+        }
+    }
+    __syncthreads();
+    bool bottom_up = false;
+    if constexpr (!kBatch) {
+        if (dir == 2) {
+            bottom_up_level(P, S, level, nxt, nslot, my_disc);
+            bottom_up = true;
+        }
+    }
+    if (!bottom_up) expand_top_down<kBatch>(P, S, L, level, my_disc);
     stage_flush<kBatch>(P, S, level, nxt, nslot);
     if (!kBatch) {
         const int wd = warp_incl_scan(my_disc);
@@ -642,9 +795,12 @@ __device__ void init_plain(const TraversalParams& P, long long tid, long long nt
         P.stats->edges = 0;
         P.stats->status = 0;
         P.stats->max_level = 0;
+        P.stats->bu_levels = 0;
     }
     const long long words = (P.n + 31) / 32;
     fill_bytes(P.visited, words * 4, 0, tid, nthreads);
+    if (P.fb[0])
+        for (int f = 0; f < 3; ++f) fill_bytes(P.fb[f], words * 4, 0, tid, nthreads);
     fill_bytes(P.dist, P.n * 4, 0xff, tid, nthreads);
     if (P.parent) fill_bytes(P.parent, P.n * 4, 0xff, tid, nthreads);
 }
@@ -661,6 +817,16 @@ __device__ void seed_plain(const TraversalParams& P, Stage<false>& S) {
     // parent = root, and queues the root in the bin of its degree
     stage_push<false>(P, S, l0, root, root, 0ull, -1, 0, 0);
     stage_flush<false>(P, S, -1, 0, 0);
+}
+
+// Per-level housekeeping of the frontier bitmaps: the bitmap the level after
+// next will fill is cleared now (it held the previous level's frontier);
+// bottom-up levels are counted.
+__device__ void prepare_level(const TraversalParams& P, int level, int dir, long long tid,
+                              long long nthreads) {
+    if (!P.fb[0]) return;
+    fill_bytes(P.fb[(level + 2) % 3], ((P.n + 31) / 32) * 4, 0, tid, nthreads);
+    if (dir == 2 && blockIdx.x == 0 && threadIdx.x == 0) P.stats->bu_levels += 1;
 }
 
 // Books the level that is about to be expanded; block 0, thread 0 only.
@@ -680,6 +846,8 @@ __device__ void book_level(const TraversalParams& P, const LevelShape& S, int le
 template <int MB>
 __global__ void __launch_bounds__(kBlock, MB)
 bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
+    extern __shared__ uint4 s_dyn[];
+    uint32_t* s_hot = reinterpret_cast<uint32_t*>(s_dyn);
     __shared__ Stage<false> s_stage[kWarps];
     Stage<false>& S = s_stage[threadIdx.x >> 5];
     stage_init(S);
@@ -689,11 +857,21 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
     if (grid_barrier(P)) {
         seed_plain(P, S);
         if (grid_barrier(P)) {
+            long long seen_edges = 0;  // edges of all frontiers so far (same in every CTA)
+            bool prev_bu = false;
             for (int level = 0;; ++level) {
                 const LevelShape L = read_level(P, level);
                 book_level(P, L, level);
-                if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) break;
-                expand_level<false>(P, S, L, level);
+                const long long nf = L.cnt[0] + L.cnt[1] + L.cnt[2];
+                if (nf == 0) break;
+                const long long mf = L.edges[0] + L.edges[1] + L.edges[2];
+                seen_edges += mf;
+                const int dir = P.fb[0] ? choose_direction(P.dir_mode, prev_bu, mf, P.nnz - seen_edges,
+                                                           nf, P.n, P.do_alpha, P.do_beta)
+                                        : 0;
+                prepare_level(P, level, dir, tid, nthreads);
+                expand_level<false>(P, S, L, level, s_hot, dir);
+                prev_bu = dir == 2;
                 if (!grid_barrier(P)) break;
             }
         }
@@ -705,6 +883,8 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
 template <int MB>
 __global__ void __launch_bounds__(kBlock, MB)
 bfs_plain_step(const __grid_constant__ TraversalParams P) {
+    extern __shared__ uint4 s_dyn[];
+    uint32_t* s_hot = reinterpret_cast<uint32_t*>(s_dyn);
     __shared__ Stage<false> s_stage[kWarps];
     Stage<false>& S = s_stage[threadIdx.x >> 5];
     stage_init(S);
@@ -718,7 +898,9 @@ bfs_plain_step(const __grid_constant__ TraversalParams P) {
         const LevelShape L = read_level(P, P.level);
         book_level(P, L, P.level);
         if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
-        expand_level<false>(P, S, L, P.level);
+        const int dir = (P.fb[0] && P.dir_override > 0) ? 2 : 0;
+        prepare_level(P, P.level, dir, tid, nthreads);
+        expand_level<false>(P, S, L, P.level, s_hot, dir);
     }
 }
 
@@ -860,7 +1042,7 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
                     break;
                 }
                 book_batch_level(P, level);
-                expand_level<true>(P, S, L, level);
+                expand_level<true>(P, S, L, level, nullptr);
                 if (!grid_barrier(P)) break;
                 sweep_batch(P, S, level, tid, nthreads);
                 if (!grid_barrier(P)) break;
@@ -891,7 +1073,7 @@ bfs_batch_step(const __grid_constant__ TraversalParams P) {
         const LevelShape L = read_level(P, P.level);
         if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
         book_batch_level(P, P.level);
-        expand_level<true>(P, S, L, P.level);
+        expand_level<true>(P, S, L, P.level, nullptr);
     } else {
         sweep_batch(P, S, P.level, tid, nthreads);
     }
@@ -912,6 +1094,36 @@ __global__ void csr_check_kernel(const int64_t* off, const int32_t* col, long lo
     for (long long v = tid; v < n; v += nthreads)
         if (off[v + 1] < off[v]) bad |= 2;
     if (bad) atomicOr(flags, bad);
+}
+
+// Symmetry test for the bottom-up step: the multiset of edges (v, u) equals
+// the multiset of reversed edges (u, v) exactly when every edge is stored in
+// both directions.  Both multisets are summed through a 64-bit mixing hash
+// (order independent, wrapping); unequal sums prove asymmetry, equal sums
+// mean symmetric up to a 2^-64-scale collision chance.
+__device__ __forceinline__ unsigned long long edge_hash(unsigned long long a, unsigned long long b) {
+    unsigned long long z = (a << 32 | b) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void symmetry_hash_kernel(const int64_t* off, const int32_t* col, long long n,
+                                     unsigned long long* sums) {
+    const long long nwarps = (long long)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    unsigned long long fwd = 0, rev = 0;
+    for (long long v = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); v < n;
+         v += nwarps) {
+        const long long b = off[v], e = off[v + 1];
+        for (long long k = b + lane; k < e; k += 32) {
+            const unsigned long long u = (unsigned)col[k];
+            fwd += edge_hash((unsigned long long)v, u);
+            rev += edge_hash(u, (unsigned long long)v);
+        }
+    }
+    atomicAdd(&sums[0], fwd);
+    atomicAdd(&sums[1], rev);
 }
 
 // Degree histogram by bin: counts[b] vertices and edges[b] entries.
@@ -964,6 +1176,12 @@ const void* batch_step_fn(int mb) {
 cudaError_t launch_csr_check(const int64_t* off, const int32_t* col, long long n, long long nnz,
                              int* flags, int sms, cudaStream_t s) {
     csr_check_kernel<<<sms * 4, 512, 0, s>>>(off, col, n, nnz, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_symmetry_hash(const int64_t* off, const int32_t* col, long long n,
+                                 unsigned long long* sums, int sms, cudaStream_t s) {
+    symmetry_hash_kernel<<<sms * 4, 256, 0, s>>>(off, col, n, sums);
     return cudaGetLastError();
 }
 

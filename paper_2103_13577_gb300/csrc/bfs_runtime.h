@@ -46,6 +46,7 @@ struct Workspace {
     LevelCtl* ctl = nullptr;
     GridBarrier* bar = nullptr;
     DevStats* stats = nullptr;
+    uint32_t* fb[3] = {nullptr, nullptr, nullptr};  // plain: frontier bitmaps
     uint64_t* lane_visited = nullptr;
     uint64_t* lane_next = nullptr;
     int32_t* roots = nullptr;          // [64]
@@ -72,7 +73,7 @@ struct bfs_graph {
     int32_t* d_new2old = nullptr;     // device numbering -> caller numbering
     int32_t* d_old2new = nullptr;     // caller numbering -> device numbering
     bool relabelled = false;
-    int32_t t_small = 32, t_large = 2048, chunk_warp = 1024, chunk_cta = 8192;
+    int32_t t_small = 32, t_large = 4096, chunk_warp = 512, chunk_cta = 2048;
     uint64_t bin_count[bfs::kBins] = {0, 0, 0};
     uint64_t bin_edges[bfs::kBins] = {0, 0, 0};
     bfs::Workspace* ws_plain = nullptr;
@@ -82,7 +83,13 @@ struct bfs_graph {
     int32_t debug_stall = 0;
     long long timeout_ns = 2000000000ll;
     int32_t use_match_any = 0;
-    int32_t min_blocks = 2;           // resident CTAs per SM the kernels are built for
+    int32_t min_blocks = 3;           // resident CTAs per SM the kernels are built for
+    int32_t hot_words = 0;            // visited words kept in shared memory on large levels
+    long long hot_min_edges = 1ll << 20;
+    int32_t dir_mode = 0;             // 0 top-down, 1 direction-optimizing, 2 bottom-up always
+    int32_t do_alpha = 15, do_beta = 18;
+    int64_t n_nonzero = 0;            // vertices with out-degree > 0
+    bool symmetric = false;           // every edge stored in both directions
     std::mutex mu;
 };
 

@@ -169,6 +169,7 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
     stats->reached = h.reached;
     stats->edges_scanned = h.edges;
     stats->status = h.status;
+    stats->bottom_up_levels = h.bu_levels;
     if (h.status == kDevTimeout) {
         set_error("bfs_run_static: device-side grid barrier wait timed out");
         return BFS_ERR_TIMEOUT;

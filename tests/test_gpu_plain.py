@@ -147,6 +147,79 @@ def test_caller_order_bins(ctx, kron16, name, bins):
     g.close()
 
 
+@pytest.mark.parametrize("hot_words", [0, 4, 1024, 16384])
+def test_shared_memory_hot_bitmap(ctx, kron16, hot_words):
+    # min edges 0: every level takes the shared-memory copy path
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col)
+    g.set_option(bfs.BFS_OPT_HOT_WORDS, hot_words)
+    g.set_option(bfs.BFS_OPT_HOT_MIN_EDGES, 0)
+    for r in roots[:8]:
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+        d2, p2, s2 = run_gpu(g, len(off) - 1, int(r), flags=bfs.BFS_HOST_LOOP)
+        assert_parity(off, col, int(r), d2, p2, s2)
+    g.close()
+
+
+DIRECTIONS = [
+    ("do_default", 1, None, None, 0),
+    ("do_eager", 1, 1 << 20, 1, 0),      # switches to bottom-up as early as possible
+    ("do_caller_order", 1, None, None, bfs.BFS_UPLOAD_NO_RELABEL),
+    ("bottom_up_always", 2, None, None, 0),
+    ("bottom_up_always_caller_order", 2, None, None, bfs.BFS_UPLOAD_NO_RELABEL),
+]
+
+
+@pytest.mark.parametrize("name,mode,alpha,beta,upflags", DIRECTIONS, ids=[d[0] for d in DIRECTIONS])
+def test_direction_optimizing(ctx, kron16, name, mode, alpha, beta, upflags):
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col, flags=upflags)
+    g.set_option(bfs.BFS_OPT_DIRECTION, mode)
+    if alpha:
+        g.set_option(bfs.BFS_OPT_DO_ALPHA, alpha)
+    if beta:
+        g.set_option(bfs.BFS_OPT_DO_BETA, beta)
+    bu_seen = 0
+    for r in roots[:10]:
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+        bu_seen += st["bottom_up_levels"]
+        d2, p2, s2 = run_gpu(g, len(off) - 1, int(r), flags=bfs.BFS_HOST_LOOP)
+        assert_parity(off, col, int(r), d2, p2, s2)
+        assert s2["bottom_up_levels"] == st["bottom_up_levels"]
+    if mode == 2:
+        assert bu_seen > 0
+    g.close()
+
+
+@pytest.mark.parametrize("graph", ["grid", "union", "directed", "er"])
+def test_bottom_up_always_other_graphs(ctx, graph):
+    if graph == "grid":
+        off, col = G.grid(60, 80)
+    elif graph == "union":
+        off, col = G.disjoint_union(G.path(100), G.star(2000))
+    elif graph == "directed":
+        off, col = G.random_graph(4000, 16000, 9, undirected=False)
+    else:
+        off, col = graphgen.erdos_renyi(14, 16, seed=5)
+    g = bfs.Graph(ctx, off, col)
+    n = len(off) - 1
+    if graph == "directed":
+        # bottom-up needs every edge stored both ways; the upload's symmetry
+        # test rejects the option on a directed graph
+        with pytest.raises(bfs.BfsError) as e:
+            g.set_option(bfs.BFS_OPT_DIRECTION, 2)
+        assert e.value.status == bfs.BFS_ERR_UNSUPPORTED
+        g.close()
+        return
+    g.set_option(bfs.BFS_OPT_DIRECTION, 2)
+    for r in (0, n // 2, n - 1):
+        dist, parent, st = run_gpu(g, n, r)
+        assert_parity(off, col, r, dist, parent, st)
+    g.close()
+
+
 def test_kron16_host_loop_and_host_outputs(ctx, kron16):
     off, col, roots = kron16
     g = bfs.Graph(ctx, off, col)
