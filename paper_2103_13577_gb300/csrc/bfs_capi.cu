@@ -527,6 +527,8 @@ static bfs_status compute_bins(bfs_graph* g, cudaStream_t s) {
     }
     g->max_degree = (int64_t)h[6];
     g->n_nonzero = (int64_t)(h[0] + h[1] + h[2]);
+    if (g->max_degree > 0x7fffffffll)
+        return fail(BFS_ERR_UNSUPPORTED, "a vertex has more than 2^31-1 adjacency entries");
     return BFS_OK;
 }
 

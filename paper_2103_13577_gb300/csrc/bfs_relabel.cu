@@ -13,7 +13,8 @@
 //   2. exclusive scan of the bucket-major count table -> tile offsets
 //   3. stable scatter: new2old[pos] = v, old2new[v] = pos
 //   4. new offsets = exclusive scan of deg[new2old[i]]
-//   5. new columns: row of new2old[i] copied with old2new applied
+//   5. new columns: row of new2old[i] copied with old2new applied, heavy
+//      neighbours first
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -96,17 +97,53 @@ __global__ void rel_newdeg_kernel(const int64_t* off, const int32_t* new2old, lo
     }
 }
 
-// One warp per new row; columns renamed through old2new.
+// One warp per new row; columns renamed through old2new and each row
+// stably partitioned into three groups by the new id of the neighbour:
+// vertices of degree >= 256, of degree >= 16, and the rest (new ids are in
+// decreasing degree-bucket order, so the groups are id ranges [0, h1),
+// [h1, h2), [h2, n)).  A bottom-up level checks neighbours in row order, and
+// the heavy neighbours first are the ones most likely in the frontier.
 __global__ void rel_columns_kernel(const int64_t* off, const int32_t* col, const int32_t* new2old,
                                    const int32_t* old2new, const int64_t* new_off, long long n,
+                                   const unsigned long long* key_start, long long ntiles,
                                    int32_t* new_col) {
+    // key = 32 - bucket, bucket = floor(log2 deg) + 1: deg >= 256 <=> key <= 23
+#ifdef BFS_NO_ROW_PARTITION
+    const long long h1 = n, h2 = n;
+#else
+    const long long h1 = (long long)key_start[24ll * ntiles];
+    const long long h2 = (long long)key_start[28ll * ntiles];
+#endif
     const long long nwarps = (long long)gridDim.x * (blockDim.x / 32);
     const int lane = threadIdx.x & 31;
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
     for (long long i = (long long)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); i < n;
          i += nwarps) {
         const int32_t o = new2old[i];
         const long long b = off[o], d = off[o + 1] - b, nb = new_off[i];
-        for (long long k = lane; k < d; k += 32) new_col[nb + k] = old2new[col[b + k]];
+        long long c0 = 0, c1 = 0;
+        for (long long k0 = 0; k0 < d; k0 += 32) {
+            const long long k = k0 + lane;
+            const int32_t x = k < d ? old2new[col[b + k]] : 0;
+            c0 += __popc(__ballot_sync(0xffffffffu, k < d && x < h1));
+            c1 += __popc(__ballot_sync(0xffffffffu, k < d && x >= h1 && x < h2));
+        }
+        long long w0 = nb, w1 = nb + c0, w2 = nb + c0 + c1;
+        for (long long k0 = 0; k0 < d; k0 += 32) {
+            const long long k = k0 + lane;
+            const int32_t x = k < d ? old2new[col[b + k]] : 0;
+            const int g = k >= d ? -1 : (x < h1 ? 0 : (x < h2 ? 1 : 2));
+            const unsigned m0 = __ballot_sync(0xffffffffu, g == 0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, g == 1);
+            const unsigned m2 = __ballot_sync(0xffffffffu, g == 2);
+            if (g == 0) new_col[w0 + __popc(m0 & lt)] = x;
+            if (g == 1) new_col[w1 + __popc(m1 & lt)] = x;
+            if (g == 2) new_col[w2 + __popc(m2 & lt)] = x;
+            w0 += __popc(m0);
+            w1 += __popc(m1);
+            w2 += __popc(m2);
+        }
     }
 }
 
@@ -229,7 +266,9 @@ cudaError_t relabel_graph(const int64_t* off, const int32_t* col, long long n, l
     rel_newdeg_kernel<<<sms * 4, 256, 0, s>>>(off, new2old, n, a);
     e = exclusive_scan_i64(a, n, new_off, tmp, s);
     if (e != cudaSuccess) return e;
-    rel_columns_kernel<<<sms * 8, 256, 0, s>>>(off, col, new2old, old2new, new_off, n, new_col);
+    rel_columns_kernel<<<sms * 8, 256, 0, s>>>(off, col, new2old, old2new, new_off, n,
+                                                reinterpret_cast<const unsigned long long*>(b), ntiles,
+                                                new_col);
     (void)nnz;
     return cudaGetLastError();
 }
