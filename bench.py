@@ -204,7 +204,7 @@ def gpu_arm(args, rank, world, local_rank):
     import paper_2103_13577_gb300 as bfs
 
     torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
+    dev_ = torch.device("cuda", local_rank)
     off, col, roots = make_workload(rank)
     n = len(off) - 1
     ctx = bfs.Context(local_rank)
@@ -213,9 +213,9 @@ def gpu_arm(args, rank, world, local_rank):
         g.set_bins(*[int(x) for x in args.bins.split(",")])
     if args.ctas_per_sm:
         g.set_option(bfs.BFS_OPT_CTAS_PER_SM, args.ctas_per_sm)
-    stream = torch.cuda.current_stream(dev)
-    dist = torch.empty(n, dtype=torch.int32, device=dev)
-    parent = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev_)
+    dist = torch.empty(n, dtype=torch.int32, device=dev_)
+    parent = torch.empty(n, dtype=torch.int32, device=dev_)
 
     def barrier():
         if world > 1:
@@ -233,9 +233,9 @@ def gpu_arm(args, rank, world, local_rank):
     for _ in range(args.warmup):
         for r in roots:
             g.run(int(r), dist, parent, stream=stream)
-    torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev_)
     barrier()
-    torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev_)
     clocks = ClockSampler(local_rank)
     clocks.start()
     time.sleep(0.25)
@@ -244,9 +244,9 @@ def gpu_arm(args, rank, world, local_rank):
         for i, r in enumerate(roots):
             g.run(int(r), dist, parent, stream=stream)
             ev[s][i + 1].record(stream)
-    torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev_)
     barrier()
-    torch.cuda.synchronize(dev)
+    torch.cuda.synchronize(dev_)
     clk = clocks.stop()
     root_ms = np.array([[ev[s][i].elapsed_time(ev[s][i + 1]) for i in range(NROOTS)]
                         for s in range(args.steps)])
@@ -257,11 +257,11 @@ def gpu_arm(args, rank, world, local_rank):
     # whole-job aggregation over ranks: root i -> sum of m_c / max time
     t_root = root_ms.mean(axis=0)
     if world > 1:
-        t_all = torch.tensor(t_root, dtype=torch.float64, device=dev)
+        t_all = torch.tensor(t_root, dtype=torch.float64, device=dev_)
         dist_mod.all_reduce(t_all, op=dist_mod.ReduceOp.MAX)
-        m_all = torch.tensor(m_c, dtype=torch.float64, device=dev)
+        m_all = torch.tensor(m_c, dtype=torch.float64, device=dev_)
         dist_mod.all_reduce(m_all, op=dist_mod.ReduceOp.SUM)
-        s_all = torch.tensor([step_ms.mean()], dtype=torch.float64, device=dev)
+        s_all = torch.tensor([step_ms.mean()], dtype=torch.float64, device=dev_)
         dist_mod.all_reduce(s_all, op=dist_mod.ReduceOp.MAX)
         t_job, m_job, ms_step = t_all.cpu().numpy(), m_all.cpu().numpy(), float(s_all.item())
     else:
@@ -284,13 +284,37 @@ def gpu_arm(args, rank, world, local_rank):
             e2e_ms[i] += (time.perf_counter() - t0) * 1e3
     e2e_ms /= e2e_steps
     if world > 1:
-        t_e = torch.tensor(e2e_ms, dtype=torch.float64, device=dev)
+        t_e = torch.tensor(e2e_ms, dtype=torch.float64, device=dev_)
         dist_mod.all_reduce(t_e, op=dist_mod.ReduceOp.MAX)
         e2e_ms = t_e.cpu().numpy()
     e2e_value = hmean(m_job / (e2e_ms * 1e-3) / 1e9)
 
+    # direction-optimizing mode on the same roots (bottom-up levels touch fewer
+    # edges; GTEPS still counts m_c, the top-down work, and is flagged so)
+    g.set_option(bfs.BFS_OPT_DIRECTION, 1)
+    for r in roots[:3]:
+        g.run(int(r), dist, parent, stream=stream)
+    do_ev = [torch.cuda.Event(enable_timing=True) for _ in range(NROOTS + 1)]
+    do_reps = max(1, min(args.steps, 3))
+    do_ms = np.zeros(NROOTS)
+    for _ in range(do_reps):
+        do_ev[0].record(stream)
+        for i, r in enumerate(roots):
+            g.run(int(r), dist, parent, stream=stream)
+            do_ev[i + 1].record(stream)
+        torch.cuda.synchronize(dev_)
+        do_ms += np.array([do_ev[i].elapsed_time(do_ev[i + 1]) for i in range(NROOTS)])
+    do_ms /= do_reps
+    do_st = g.sync(stream)
+    g.set_option(bfs.BFS_OPT_DIRECTION, 0)
+    if world > 1:
+        t_d = torch.tensor(do_ms, dtype=torch.float64, device=dev_)
+        dist_mod.all_reduce(t_d, op=dist_mod.ReduceOp.MAX)
+        do_ms = t_d.cpu().numpy()
+    do_value = hmean(m_job / (do_ms * 1e-3) / 1e9)
+
     # 64-root batched launch on the same graph (one persistent launch)
-    bd = torch.empty((NROOTS, n), dtype=torch.int32, device=dev)
+    bd = torch.empty((NROOTS, n), dtype=torch.int32, device=dev_)
     for _ in range(2):
         g.run_batch(roots, bd, stream=stream)
     bst = g.batch_sync(stream)
@@ -343,6 +367,11 @@ def gpu_arm(args, rank, world, local_rank):
                          if peak_kind == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": float(alg_bytes.mean())},
             "cpu_baseline": cpu,
+            "direction_optimizing": {
+                "value": do_value, "unit": "GTEPS", "root_ms_median": float(np.median(do_ms)),
+                "bottom_up_levels_last_root": int(do_st["bottom_up_levels"]),
+                "note": "BFS_OPT_DIRECTION=1; GTEPS counts m_c (the top-down edge work), "
+                        "bottom-up levels examine fewer edges"},
             "batched": {"roots": NROOTS, "ms": batch_ms, "gteps": batch_gteps,
                         "edges": int(bst["edges_scanned"]), "levels": int(bst["levels"]),
                         "speedup_vs_plain_step": ms_step / batch_ms},
