@@ -142,7 +142,7 @@ size_t workspace_bytes(const bfs_graph* g, bool batched, int /*nlanes*/) {
         if (batched) per += round_up(cap * 8, kAlign);
         b += 2 * per;
     }
-    if (batched) b += 2 * round_up((size_t)g->n * 8, kAlign);
+    if (batched) b += 2 * round_up((size_t)g->n * 8, kAlign) + round_up((size_t)g->n * 64, kAlign);
     return b;
 }
 
@@ -166,6 +166,7 @@ void free_workspace(bfs_graph* g, Workspace* ws) {
     m->release(ws->control);
     m->release(ws->lane_visited);
     m->release(ws->lane_next);
+    m->release(ws->lane_level);
     m->release(ws->dist_scratch);
     m->release(ws->parent_scratch);
     m->release(ws->batch_dist_scratch);
@@ -209,6 +210,7 @@ Workspace* make_workspace(bfs_graph* g, DeviceAllocator* m, bool batched, cudaSt
     if (batched) {
         ws->lane_visited = static_cast<uint64_t*>(get((size_t)g->n * 8));
         ws->lane_next = static_cast<uint64_t*>(get((size_t)g->n * 8));
+        ws->lane_level = static_cast<uint8_t*>(get((size_t)g->n * 64));
     }
     if (!ok) {
         free_workspace(g, ws);
@@ -248,6 +250,7 @@ static void fill_params(bfs_graph* g, Workspace* ws, TraversalParams& P) {
     P.stats = ws->stats;
     P.lane_visited = ws->lane_visited;
     P.lane_next = ws->lane_next;
+    P.lane_level = ws->lane_level;
     P.timeout_ns = g->timeout_ns;
     P.debug_stall = g->debug_stall;
     P.use_match_any = g->use_match_any;
@@ -407,7 +410,8 @@ bfs_status run_batch_on(bfs_graph* g, Workspace* ws, const int32_t* roots, int32
             if (e != cudaSuccess) return cuda_fail(e, "level count");
         }
     }
-    return BFS_OK;
+    P.phase = 4;  // distance rows in the caller's numbering
+    return launch_plain_kernel(batch_step_fn(g->min_blocks), grid, P, s);
 }
 
 static bfs_status finish(Workspace* ws, cudaStream_t s, bfs_run_stats* out) {

@@ -76,6 +76,7 @@ struct TraversalParams {
     // batched traversal state
     uint64_t* lane_visited;   // [n]
     uint64_t* lane_next;      // [n]
+    uint8_t* lane_level;      // [n][64]: level of each lane at each vertex
     int32_t nlanes;
     int32_t dist_int8;
     int32_t roots[64];        // caller numbering, [nlanes]

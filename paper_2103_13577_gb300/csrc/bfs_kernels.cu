@@ -930,16 +930,50 @@ __device__ void init_batch(const TraversalParams& P, long long tid, long long nt
     }
     fill_u64(P.lane_visited, P.n, tid, nthreads);
     fill_u64(P.lane_next, P.n, tid, nthreads);
-    const long long total = (long long)P.nlanes * P.n;
-    fill_bytes(P.dist, total * (P.dist_int8 ? 1 : 4), 0xff, tid, nthreads);
+    // distances are not filled here: emit_batch writes every (lane, vertex)
 }
 
-__device__ __forceinline__ void write_lane_dist(const TraversalParams& P, int lane_idx,
-                                                int32_t cv, int value) {
-    const long long idx = (long long)lane_idx * P.n + cv;
-    if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)value;
-    else P.dist[idx] = value;
+// Level of lane i at vertex v, one byte per lane in a vertex-major array
+// (64 bytes per vertex): a sweep's writes for one vertex stay inside its own
+// two sectors.  255 means "level >= 255, written straight into dist".
+__device__ __forceinline__ void record_lane_level(const TraversalParams& P, int lane_idx,
+                                                  long long v, int32_t cv, int level) {
+    if (level < 255) {
+        P.lane_level[v * 64 + lane_idx] = (uint8_t)level;
+    } else {
+        P.lane_level[v * 64 + lane_idx] = 255;
+        const long long idx = (long long)lane_idx * P.n + cv;
+        if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)level;
+        else P.dist[idx] = level;
+    }
 }
+
+// After the last level: dist rows in the caller's numbering, one thread per
+// caller vertex (coalesced stores in every row); unreached lanes get -1.
+__device__ void emit_batch(const TraversalParams& P, long long tid, long long nthreads) {
+    for (long long c = tid; c < P.n; c += nthreads) {
+        const long long v = P.old2new ? __ldg(P.old2new + c) : c;
+        const uint64_t vis = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_visited) + v);
+        const uint4* lv = reinterpret_cast<const uint4*>(P.lane_level + v * 64);
+        uint4 q[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0),
+                      make_uint4(0, 0, 0, 0)};
+        if (vis) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = __ldcg(lv + k);
+        }
+        const uint8_t* bytes = reinterpret_cast<const uint8_t*>(q);
+        for (int i = 0; i < P.nlanes; ++i) {
+            const bool hit = (vis >> i) & 1ull;
+            const int lvl = bytes[i];
+            if (hit && lvl == 255) continue;  // deep level, already written
+            const int val = hit ? lvl : -1;
+            const long long idx = (long long)i * P.n + c;
+            if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)val;
+            else P.dist[idx] = val;
+        }
+    }
+}
+
 
 // One warp seeds all roots: duplicates share one queue entry whose mask
 // holds every lane with that root.
@@ -961,7 +995,7 @@ __device__ void seed_batch(const TraversalParams& P, Stage<true>& S) {
                 }
             }
             r = P.old2new ? __ldg(P.old2new + cr) : cr;
-            write_lane_dist(P, i, cr, 0);
+            record_lane_level(P, i, r, cr, 0);
             if (first) P.lane_visited[r] = mask;
         }
         stage_push<true>(P, S, first, r, 0, mask, -1, 0, 0);
@@ -1004,11 +1038,12 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) any |= __shfl_xor_sync(FULL_MASK, any, d);
         if (any != 0ull) {
-            const int32_t cv = (fresh != 0ull) ? (P.new2old ? __ldg(P.new2old + v) : (int32_t)v) : 0;
+            const int32_t cv =
+                (fresh != 0ull && level + 1 >= 255) ? (P.new2old ? __ldg(P.new2old + v) : (int32_t)v) : 0;
             while (any != 0ull) {
                 const int li = __ffsll((long long)any) - 1;
                 any &= any - 1ull;
-                if ((fresh >> li) & 1ull) write_lane_dist(P, li, cv, level + 1);
+                if ((fresh >> li) & 1ull) record_lane_level(P, li, v, cv, level + 1);
             }
         }
         stage_push<true>(P, S, fresh != 0ull, (int32_t)(v < P.n ? v : 0), 0, fresh, level, nxt,
@@ -1065,6 +1100,9 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
                         P.stats->levels = level + 2;
                 }
             }
+            // every sweep is complete here (the loop exits right after a barrier
+            // or before any expansion of an empty level)
+            if (ld_volatile_i32(&P.stats->abort) == 0) emit_batch(P, tid, nthreads);
         }
     }
     kernel_exit(P);
@@ -1087,8 +1125,10 @@ bfs_batch_step(const __grid_constant__ TraversalParams P) {
         if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
         book_batch_level(P, P.level);
         expand_level<true>(P, S, L, P.level, nullptr);
-    } else {
+    } else if (P.phase == 3) {
         sweep_batch(P, S, P.level, tid, nthreads);
+    } else {
+        emit_batch(P, tid, nthreads);
     }
 }
 

@@ -114,6 +114,20 @@ def test_batch_int8_depth_overflow(ctx):
     g.close()
 
 
+def test_batch_deep_graph_int32(ctx):
+    # levels beyond 254 take the direct-write path of the level records
+    off, col = G.path(700)
+    roots = np.array([0, 350, 699, 0], dtype=np.int32)
+    g = bfs.Graph(ctx, off, col)
+    d, st = batch_gpu(g, 700, roots)
+    ref, _ = expected(off, col, roots)
+    assert np.array_equal(d, ref)
+    assert st["levels"] == 700
+    dl, _ = batch_gpu(g, 700, roots, flags=bfs.BFS_HOST_LOOP)
+    assert np.array_equal(dl, ref)
+    g.close()
+
+
 def test_batch_equals_plain_runs(ctx):
     off, col = graphgen.erdos_renyi(13, 16, seed=8)
     n = len(off) - 1
