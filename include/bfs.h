@@ -155,6 +155,28 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
 #define BFS_OPT_DO_BETA         8
 bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value);
 
+/* ---- autotuning -----------------------------------------------------------------
+ * Picks t_small, t_large, the base chunk sizes and BFS_OPT_CTAS_PER_SM for g
+ * by coordinate descent (one knob at a time over a short candidate list,
+ * two passes), timing each candidate with CUDA events on the sample roots
+ * (host array, 1..64 entries, caller numbering): single-source runs, or one
+ * batched launch with BFS_TUNE_BATCHED.  The best setting is applied to g.
+ * cache_path (nullable) names a JSON-lines file: a graph whose fingerprint
+ * (counts plus a hash of sampled offsets and columns) and flags are found
+ * there is set up without timing; otherwise the result is appended.  Must not
+ * run while other traversals on g are in flight.  The paper has no
+ * autotuner; its per-bin launch sizes are fixed by the bin's degree bound. */
+#define BFS_TUNE_BATCHED 0x1u
+typedef struct bfs_tune_result {
+    int32_t t_small, t_large, chunk_warp, chunk_cta, ctas_per_sm;
+    int32_t from_cache;     /* 1 when the setting came from cache_path */
+    int32_t trials;         /* candidates timed */
+    double best_ms;         /* time of the chosen setting over the sample (-1 if cached) */
+    uint64_t fingerprint;
+} bfs_tune_result;
+bfs_status bfs_graph_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots, uint32_t flags,
+                              const char* cache_path, bfs_tune_result* out);
+
 /* ---- single-source traversal ----------------------------------------------
  * Algorithm 1 / Algorithm 2 Phase 1 (one compute node) from `root` (caller
  * numbering).  dist: int32[n]; parent: int32[n] or NULL.  Device pointers by

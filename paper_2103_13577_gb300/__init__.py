@@ -34,6 +34,7 @@ from ._lib import (  # noqa: F401
     BFS_OK,
     BFS_OUT_HOST,
     BFS_PENDING,
+    BFS_TUNE_BATCHED,
     BFS_UPLOAD_DEVICE_PTRS,
     BFS_UPLOAD_NO_RELABEL,
     BfsError,
@@ -47,6 +48,7 @@ from .api import (  # noqa: F401
     bfs_batch_sync,
     bfs_context_create,
     bfs_context_destroy,
+    bfs_graph_autotune,
     bfs_graph_free,
     bfs_graph_get_info,
     bfs_graph_set_bins,

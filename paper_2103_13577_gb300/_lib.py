@@ -29,6 +29,7 @@ BFS_UPLOAD_NO_RELABEL = 0x2
 BFS_OUT_HOST = 0x1
 BFS_DIST_INT8 = 0x2
 BFS_HOST_LOOP = 0x4
+BFS_TUNE_BATCHED = 0x1
 BFS_OPT_WARP_AGGREGATE = 1
 BFS_OPT_TIMEOUT_NS = 2
 BFS_OPT_CTAS_PER_SM = 3
@@ -59,6 +60,14 @@ class RunStats(ctypes.Structure):
                 ("bottom_up_levels", ctypes.c_int32)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("t_small", ctypes.c_int32), ("t_large", ctypes.c_int32),
+                ("chunk_warp", ctypes.c_int32), ("chunk_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("from_cache", ctypes.c_int32),
+                ("trials", ctypes.c_int32), ("best_ms", ctypes.c_double),
+                ("fingerprint", ctypes.c_uint64)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("launches", ctypes.c_int64),
@@ -82,6 +91,7 @@ SIGNATURES = {
     "bfs_graph_set_bins": (_i32, [_vp, _i32, _i32, _i32, _i32]),
     "bfs_graph_set_option": (_i32, [_vp, _i32, _i64]),
     "bfs_run": (_i32, [_vp, _i32, _vp, _vp, _vp, _u32]),
+    "bfs_graph_autotune": (_i32, [_vp, _vp, _i32, _u32, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
     "bfs_graph_sync": (_i32, [_vp, _vp, ctypes.POINTER(RunStats)]),
     "bfs_run_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _u32]),
     "bfs_batch_sync": (_i32, [_vp, _vp, ctypes.POINTER(RunStats)]),

@@ -14,8 +14,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (BFS_DIST_INT8, BFS_OUT_HOST, BFS_UPLOAD_DEVICE_PTRS, GraphInfo, RunStats,
-                   ServerStats, check)
+from ._lib import (BFS_DIST_INT8, BFS_OUT_HOST, BFS_TUNE_BATCHED, BFS_UPLOAD_DEVICE_PTRS,
+                   GraphInfo, RunStats, ServerStats, TuneResult, check)
 
 
 def _is_torch(x) -> bool:
@@ -108,6 +108,16 @@ def bfs_graph_set_bins(g: int, t_small: int, t_large: int, chunk_warp: int, chun
 
 def bfs_graph_set_option(g: int, option: int, value: int) -> None:
     check(_lib.lib().bfs_graph_set_option(g, option, int(value)), "bfs_graph_set_option")
+
+
+def bfs_graph_autotune(g: int, roots, batched: bool = False, cache_path: str | None = None) -> dict:
+    roots = np.ascontiguousarray(roots, dtype=np.int32)
+    res = TuneResult()
+    check(_lib.lib().bfs_graph_autotune(g, roots.ctypes.data, len(roots),
+                                        BFS_TUNE_BATCHED if batched else 0,
+                                        cache_path.encode() if cache_path else None,
+                                        ctypes.byref(res)), "bfs_graph_autotune")
+    return {f: getattr(res, f) for f, _ in TuneResult._fields_}
 
 
 def bfs_run(g: int, root: int, dist, parent=None, stream=None, flags: int = 0) -> None:
@@ -246,6 +256,9 @@ class Graph:
 
     def set_bins(self, t_small, t_large, chunk_warp, chunk_cta):
         bfs_graph_set_bins(self.handle, t_small, t_large, chunk_warp, chunk_cta)
+
+    def autotune(self, roots, batched: bool = False, cache_path: str | None = None) -> dict:
+        return bfs_graph_autotune(self.handle, roots, batched, cache_path)
 
     def set_option(self, option: int, value: int):
         bfs_graph_set_option(self.handle, option, value)
