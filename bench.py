@@ -197,6 +197,27 @@ def reference_arm(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+def aggregate_ranks(t_root, m_c, step_ms, world, device):
+    """Whole-job numbers over ranks: root slot i takes the slowest rank's
+    time and the sum of the ranks' m_c; the step time is the slowest rank's.
+    Returns (per-root times, per-root edges, ms per step, hmean GTEPS)."""
+    import torch
+    import torch.distributed as dist_mod
+    if world > 1:
+        t_all = torch.tensor(t_root, dtype=torch.float64, device=device)
+        dist_mod.all_reduce(t_all, op=dist_mod.ReduceOp.MAX)
+        m_all = torch.tensor(np.asarray(m_c, dtype=np.float64), dtype=torch.float64, device=device)
+        dist_mod.all_reduce(m_all, op=dist_mod.ReduceOp.SUM)
+        s_all = torch.tensor([float(np.mean(step_ms))], dtype=torch.float64, device=device)
+        dist_mod.all_reduce(s_all, op=dist_mod.ReduceOp.MAX)
+        t_job, m_job, ms_step = t_all.cpu().numpy(), m_all.cpu().numpy(), float(s_all.item())
+    else:
+        t_job = np.asarray(t_root, dtype=np.float64)
+        m_job = np.asarray(m_c, dtype=np.float64)
+        ms_step = float(np.mean(step_ms))
+    return t_job, m_job, ms_step, hmean(m_job / (t_job * 1e-3) / 1e9)
+
+
 def gpu_arm(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist_mod
@@ -254,20 +275,8 @@ def gpu_arm(args, rank, world, local_rank):
     st = g.sync(stream)
     assert st["status"] == 0
 
-    # whole-job aggregation over ranks: root i -> sum of m_c / max time
     t_root = root_ms.mean(axis=0)
-    if world > 1:
-        t_all = torch.tensor(t_root, dtype=torch.float64, device=dev_)
-        dist_mod.all_reduce(t_all, op=dist_mod.ReduceOp.MAX)
-        m_all = torch.tensor(m_c, dtype=torch.float64, device=dev_)
-        dist_mod.all_reduce(m_all, op=dist_mod.ReduceOp.SUM)
-        s_all = torch.tensor([step_ms.mean()], dtype=torch.float64, device=dev_)
-        dist_mod.all_reduce(s_all, op=dist_mod.ReduceOp.MAX)
-        t_job, m_job, ms_step = t_all.cpu().numpy(), m_all.cpu().numpy(), float(s_all.item())
-    else:
-        t_job, m_job, ms_step = t_root, m_c.astype(np.float64), float(step_ms.mean())
-    gteps_root = m_job / (t_job * 1e-3) / 1e9
-    value = hmean(gteps_root)
+    t_job, m_job, ms_step, value = aggregate_ranks(t_root, m_c, step_ms, world, dev_)
 
     # e2e: the public call with host outputs (copies inside the timed region)
     h_dist = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy()
@@ -383,6 +392,218 @@ def gpu_arm(args, rank, world, local_rank):
     ctx.close()
 
 
+# ------------------------------------------------- batched configuration
+def batched_arm(args):
+    """64 roots in one launch vs 64 single-source runs, on a Kronecker graph
+    (scale 24, edge factor 16) and an Erdos-Renyi graph (2^24 vertices,
+    average degree 32), each autotuned first (plain and batched separately)."""
+    import torch
+
+    import graphgen
+    import paper_2103_13577_gb300 as bfs
+
+    scale = args.batch_scale
+    out = {"metric": METRIC, "unit": "GTEPS", "workload": f"batched_64roots_s{scale}",
+           "higher_is_better": True, "data": "synthetic", "dtype": "int32", "graphs": []}
+    ctx = bfs.Context(0)
+    stream = torch.cuda.current_stream()
+    for name, gen in (("kronecker", lambda: graphgen.kronecker(scale, 16, seed=24)),
+                      ("erdos_renyi", lambda: graphgen.erdos_renyi(scale, 32, seed=25))):
+        t0 = time.time()
+        off, col = gen()
+        gen_s = time.time() - t0
+        n = len(off) - 1
+        roots = graphgen.pick_roots(off, NROOTS, seed=ROOT_SEED)
+        g = bfs.Graph(ctx, off, col)
+        dist = torch.empty(n, dtype=torch.int32, device="cuda")
+        parent = torch.empty(n, dtype=torch.int32, device="cuda")
+        rec = {"graph": name, "vertices": n, "directed_entries": int(len(col)), "gen_s": gen_s}
+        tune_plain = g.autotune(roots[:4])
+        rec["tuned_plain"] = {k: tune_plain[k] for k in ("t_small", "t_large", "chunk_warp", "chunk_cta", "ctas_per_sm")}
+
+        def time_plain(direction):
+            g.set_option(bfs.BFS_OPT_DIRECTION, direction)
+            for r in roots[:3]:
+                g.run(int(r), dist, parent, stream=stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
+            for r in roots:
+                g.run(int(r), dist, parent, stream=stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            g.set_option(bfs.BFS_OPT_DIRECTION, 0)
+            return ev[0].elapsed_time(ev[1])
+
+        m_c = 0
+        for r in roots:
+            g.run(int(r), dist, None, stream=stream)
+            m_c += g.sync(stream)["edges_scanned"]
+        plain_ms = time_plain(0)
+        do_ms = time_plain(1)
+        tune_b = g.autotune(roots, batched=True)
+        rec["tuned_batched"] = {k: tune_b[k] for k in ("t_small", "t_large", "chunk_warp", "chunk_cta", "ctas_per_sm")}
+        res = {}
+        for dt_name, dt in (("int32", torch.int32), ("int8", torch.int8)):
+            bd = torch.empty((NROOTS, n), dtype=dt, device="cuda")
+            g.run_batch(roots, bd, stream=stream)
+            bst = g.batch_sync(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            reps = 3
+            ev[0].record(stream)
+            for _ in range(reps):
+                g.run_batch(roots, bd, stream=stream)
+            ev[1].record(stream)
+            bst = g.batch_sync(stream)
+            ms = ev[0].elapsed_time(ev[1]) / reps
+            res[dt_name] = {"ms": ms, "gteps": bst["edges_scanned"] / (ms * 1e-3) / 1e9,
+                            "levels": int(bst["levels"])}
+            del bd
+        rec.update({"sum_m_c": int(m_c), "plain_64_runs_ms": plain_ms,
+                    "plain_gteps_aggregate": m_c / (plain_ms * 1e-3) / 1e9,
+                    "direction_optimizing_64_runs_ms": do_ms,
+                    "direction_optimizing_gteps_aggregate": m_c / (do_ms * 1e-3) / 1e9,
+                    "batched": res,
+                    "batched_speedup_vs_plain": plain_ms / res["int32"]["ms"],
+                    "batched_speedup_vs_direction_optimizing": do_ms / res["int32"]["ms"]})
+        out["graphs"].append(rec)
+        g.close()
+        del dist, parent
+        torch.cuda.empty_cache()
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------- serving configuration
+def serve_arm(args):
+    """Served single-root queries on four resident Kronecker graphs (scales
+    18, 20, 22, 24, edge factor 16): seeded Poisson arrivals at each offered
+    rate, graph uniform, root uniform among degree >= 1 vertices; the server
+    packs same-graph queries into batched launches on 4 streams within a
+    fixed memory budget.  Latency = completion on the server's monotonic
+    clock minus the scheduled arrival; the result copy to the caller's pinned
+    host buffer is inside it.  Baseline: the same arrivals served one at a
+    time by bfs_run (FIFO, arrival order), from measured per-graph service
+    times."""
+    import queue as queue_mod
+
+    import torch
+
+    import graphgen
+    import paper_2103_13577_gb300 as bfs
+
+    scales = [int(x) for x in args.serve_scales.split(",")]
+    ctx = bfs.Context(0)
+    graphs = []
+    for sc in scales:
+        off, col = graphgen.kronecker(sc, 16, seed=100 + sc)
+        g = bfs.Graph(ctx, off, col)
+        pool_roots = graphgen.pick_roots(off, 256, seed=200 + sc)
+        graphs.append({"scale": sc, "n": len(off) - 1, "g": g, "roots": pool_roots,
+                       "off": off, "col": col})
+    srv = bfs.Server(ctx, args.serve_budget << 30, num_streams=4)
+    for gr in graphs:
+        gr["gid"] = srv.add_graph(gr["g"])
+        nbuf = int(max(8, min(256, (2 << 30) // (gr["n"] * 4))))
+        gr["pool"] = queue_mod.Queue()
+        for _ in range(nbuf):
+            gr["pool"].put(torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy())
+
+    # baseline service times: bfs_run with a pinned host output, per graph
+    svc = []
+    for gr in graphs:
+        h = torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy()
+        for r in gr["roots"][:3]:
+            gr["g"].run(int(r), h)
+        ts = []
+        for r in gr["roots"][3:19]:
+            t0 = time.perf_counter()
+            gr["g"].run(int(r), h)
+            ts.append(time.perf_counter() - t0)
+        svc.append(float(np.mean(ts)))
+
+    results = []
+    for rate in [int(x) for x in args.serve_rates.split(",")]:
+        nq = int(min(args.serve_max_queries, rate * args.serve_window))
+        rng = np.random.default_rng(rate)
+        gaps = rng.exponential(1.0 / rate, nq)
+        which = rng.integers(0, len(graphs), nq)
+        ridx = rng.integers(0, 256, nq)
+        t0 = time.monotonic_ns() + 20_000_000
+        arrival = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
+        tickets = [None] * nq
+        bufs = [None] * nq
+        done = np.zeros(nq, dtype=np.int64)
+        submitted = queue_mod.Queue()
+        errors = []
+
+        def collector():
+            for _ in range(nq):
+                i = submitted.get()
+                gr = graphs[which[i]]
+                st = srv.wait(tickets[i], 60_000_000)
+                stat, _, _, dn = srv.times(tickets[i])
+                if stat != bfs.BFS_OK:
+                    errors.append(stat)
+                done[i] = dn
+                srv.release(tickets[i])
+                gr["pool"].put(bufs[i])
+
+        th = threading.Thread(target=collector)
+        th.start()
+        for i in range(nq):
+            gr = graphs[which[i]]
+            while True:
+                now = time.monotonic_ns()
+                if now >= arrival[i]:
+                    break
+                if arrival[i] - now > 300_000:
+                    time.sleep((arrival[i] - now - 200_000) / 1e9)
+            bufs[i] = gr["pool"].get()
+            tickets[i] = srv.submit(gr["gid"], int(gr["roots"][ridx[i]]), bufs[i])
+            submitted.put(i)
+        th.join()
+        lat_ms = (done - arrival) / 1e6
+        span_s = (done.max() - arrival[0]) / 1e9
+        # FIFO model of the same arrivals served one query at a time
+        end = 0.0
+        base_lat = np.empty(nq)
+        arr_s = (arrival - arrival[0]) / 1e9
+        for i in range(nq):
+            start = max(arr_s[i], end)
+            end = start + svc[which[i]]
+            base_lat[i] = (end - arr_s[i]) * 1e3
+        results.append({
+            "offered_qps": rate, "queries": nq, "errors": len(errors),
+            "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "sustained_qps": nq / span_s,
+            "plain_fifo_p50_ms": float(np.percentile(base_lat, 50)),
+            "plain_fifo_p99_ms": float(np.percentile(base_lat, 99)),
+            "plain_fifo_qps": nq / (end if end > 0 else 1.0),
+        })
+    st = srv.stats()
+    # spot-check a few served results against single-source runs
+    check_ok = True
+    for gr in graphs:
+        h = torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy()
+        ref = torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy()
+        r = int(gr["roots"][0])
+        t = srv.submit(gr["gid"], r, h)
+        srv.wait(t, 60_000_000)
+        srv.release(t)
+        gr["g"].run(r, ref)
+        check_ok = check_ok and bool(np.array_equal(h, ref))
+    srv.close()
+    out = {"metric": METRIC, "workload": "served_queries_kronecker_s" + "_".join(map(str, scales)),
+           "unit": "ms", "data": "synthetic", "memory_budget_gib": args.serve_budget,
+           "streams": 4, "window_s": args.serve_window, "rates": results,
+           "plain_service_ms": {f"s{gr['scale']}": t * 1e3 for gr, t in zip(graphs, svc)},
+           "server": st, "served_equals_single_source": check_ok}
+    for gr in graphs:
+        gr["g"].close()
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -393,6 +614,15 @@ def main():
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--serve-scales", default="18,20,22,24")
+    ap.add_argument("--serve-rates", default="1000,10000,50000")
+    ap.add_argument("--serve-window", type=float, default=1.0)
+    ap.add_argument("--serve-max-queries", type=int, default=20000)
+    ap.add_argument("--serve-budget", type=int, default=32, help="GiB")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serve"],
+                    help="plain: the headline line (default); batched: the 64-root batched "
+                         "configuration on Kronecker and Erdos-Renyi graphs")
+    ap.add_argument("--batch-scale", type=int, default=24)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     rank = env_int("RANK", 0)
@@ -400,6 +630,14 @@ def main():
     local_rank = env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
         reference_arm(args, rank, world)
+        return
+    if args.workload == "batched":
+        if rank == 0:
+            batched_arm(args)
+        return
+    if args.workload == "serve":
+        if rank == 0:
+            serve_arm(args)
         return
     if world > 1:
         import torch

@@ -238,6 +238,11 @@ bfs_status bfs_poll(bfs_server* s, bfs_ticket ticket);
 bfs_status bfs_wait(bfs_server* s, bfs_ticket ticket, int64_t timeout_us);
 /* Forget a finished ticket. */
 bfs_status bfs_release(bfs_server* s, bfs_ticket ticket);
+/* Timestamps of a ticket on the monotonic clock (CLOCK_MONOTONIC, ns):
+ * submission, launch of the batch that carried it, and completion as seen
+ * by the server (0 while not reached).  Returns the ticket's status. */
+bfs_status bfs_ticket_times(bfs_server* s, bfs_ticket ticket, int64_t* submit_ns,
+                            int64_t* launch_ns, int64_t* done_ns);
 
 typedef struct bfs_server_stats {
     int64_t submitted, completed, failed;

@@ -65,5 +65,6 @@ from .api import (  # noqa: F401
     bfs_server_destroy,
     bfs_server_get_stats,
     bfs_submit,
+    bfs_ticket_times,
     bfs_wait,
 )

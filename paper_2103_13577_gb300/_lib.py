@@ -101,6 +101,8 @@ SIGNATURES = {
     "bfs_poll": (_i32, [_vp, _i64]),
     "bfs_wait": (_i32, [_vp, _i64, _i64]),
     "bfs_release": (_i32, [_vp, _i64]),
+    "bfs_ticket_times": (_i32, [_vp, _i64, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                ctypes.POINTER(_i64)]),
     "bfs_server_get_stats": (_i32, [_vp, ctypes.POINTER(ServerStats)]),
     "bfs_server_destroy": (_i32, [_vp]),
     "bfs_last_error": (ctypes.c_char_p, []),

@@ -206,6 +206,14 @@ def bfs_wait(s: int, ticket: int, timeout_us: int = -1) -> int:
     return check(_lib.lib().bfs_wait(s, ticket, timeout_us), "bfs_wait")
 
 
+def bfs_ticket_times(s: int, ticket: int) -> tuple[int, int, int, int]:
+    """(status, submit_ns, launch_ns, done_ns) on the monotonic clock."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    st = check(_lib.lib().bfs_ticket_times(s, ticket, ctypes.byref(a), ctypes.byref(b),
+                                           ctypes.byref(c)), "bfs_ticket_times")
+    return st, a.value, b.value, c.value
+
+
 def bfs_release(s: int, ticket: int) -> None:
     check(_lib.lib().bfs_release(s, ticket), "bfs_release")
 
@@ -299,6 +307,9 @@ class Server:
 
     def release(self, ticket: int) -> None:
         bfs_release(self.handle, ticket)
+
+    def times(self, ticket: int) -> tuple[int, int, int, int]:
+        return bfs_ticket_times(self.handle, ticket)
 
     def stats(self) -> dict:
         return bfs_server_get_stats(self.handle)

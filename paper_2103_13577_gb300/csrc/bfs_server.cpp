@@ -27,12 +27,19 @@
 
 namespace bfs {
 
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
 struct Query {
     bfs_ticket ticket = 0;
     int32_t graph_id = 0;
     int32_t root = 0;
     int32_t* dist_out = nullptr;
     bfs_status status = BFS_PENDING;
+    int64_t submit_ns = 0, launch_ns = 0, done_ns = 0;
 };
 
 struct Launch {
@@ -112,9 +119,11 @@ static bool try_launch(bfs_server* s) {
         L.ws = ws;
         L.d_dist = d_dist;
         std::vector<int32_t> roots;
+        const int64_t t_launch = now_ns();
         for (int i = 0; i < k; ++i) {
             L.lanes.push_back(q.front());
             roots.push_back(q.front()->root);
+            q.front()->launch_ns = t_launch;
             q.pop_front();
         }
         // a share of the persistent grid so that launches on other slots
@@ -173,7 +182,11 @@ static int reap(bfs_server* s, bool block) {
         bfs_status st = BFS_OK;
         if (e != cudaSuccess) st = cuda_fail(e, "batched traversal");
         if (st == BFS_OK) st = batch_finish(s->graphs[L.graph_id], L.ws, s->slots[L.slot].stream, nullptr);
-        for (auto& q : L.lanes) q->status = st;
+        const int64_t t_done = now_ns();
+        for (auto& q : L.lanes) {
+            q->status = st;
+            q->done_ns = t_done;
+        }
         if (st == BFS_OK) s->stats.completed += (int64_t)L.lanes.size();
         else s->stats.failed += (int64_t)L.lanes.size();
         free_workspace(s->graphs[L.graph_id], L.ws);
@@ -311,6 +324,7 @@ bfs_status bfs_submit(bfs_server* s, int32_t graph_id, int32_t root, int32_t* di
     q->graph_id = graph_id;
     q->root = root;
     q->dist_out = dist_out;
+    q->submit_ns = now_ns();
     s->tickets[q->ticket] = q;
     s->pending[(size_t)graph_id].push_back(q);
     s->stats.submitted += 1;
@@ -349,6 +363,25 @@ bfs_status bfs_wait(bfs_server* s, bfs_ticket ticket, int64_t timeout_us) {
     if (timeout_us < 0) s->cv_done.wait(lk, ready);
     else s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
     return q->status;
+}
+
+bfs_status bfs_ticket_times(bfs_server* s, bfs_ticket ticket, int64_t* submit_ns,
+                            int64_t* launch_ns, int64_t* done_ns) {
+    if (!s) {
+        set_error("null server");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) {
+        set_error("unknown ticket");
+        return BFS_ERR_NOT_FOUND;
+    }
+    const Query& q = *it->second;
+    if (submit_ns) *submit_ns = q.submit_ns;
+    if (launch_ns) *launch_ns = q.launch_ns;
+    if (done_ns) *done_ns = q.done_ns;
+    return q.status;
 }
 
 bfs_status bfs_release(bfs_server* s, bfs_ticket ticket) {
