@@ -144,7 +144,13 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *                            symmetric graph (bottom-up follows a vertex's own
  *                            adjacency); the upload tests symmetry and other
  *                            graphs refuse them with BFS_ERR_UNSUPPORTED.
- *   BFS_OPT_DO_ALPHA, BFS_OPT_DO_BETA   the two thresholds (default 15, 18). */
+ *   BFS_OPT_DO_ALPHA, BFS_OPT_DO_BETA   the two thresholds (default 15, 18).
+ *   BFS_OPT_BITMAP_FRONTIER  d > 0: a top-down level whose frontier holds more
+ *                            than n / d vertices reads its light bin (deg <
+ *                            t_small) from the frontier bitmap in vertex order
+ *                            (tiles of 1024 vertices per warp) instead of that
+ *                            bin's queue; the heavier bins keep their queues.
+ *                            0: never (default). */
 #define BFS_OPT_WARP_AGGREGATE  1
 #define BFS_OPT_TIMEOUT_NS      2
 #define BFS_OPT_CTAS_PER_SM     3
@@ -153,6 +159,7 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
 #define BFS_OPT_DIRECTION       6
 #define BFS_OPT_DO_ALPHA        7
 #define BFS_OPT_DO_BETA         8
+#define BFS_OPT_BITMAP_FRONTIER 9
 bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value);
 
 /* ---- autotuning -----------------------------------------------------------------

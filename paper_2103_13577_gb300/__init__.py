@@ -23,6 +23,7 @@ from ._lib import (  # noqa: F401
     BFS_ERR_TIMEOUT,
     BFS_ERR_UNSUPPORTED,
     BFS_HOST_LOOP,
+    BFS_OPT_BITMAP_FRONTIER,
     BFS_OPT_CTAS_PER_SM,
     BFS_OPT_DIRECTION,
     BFS_OPT_DO_ALPHA,

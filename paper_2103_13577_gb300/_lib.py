@@ -38,6 +38,7 @@ BFS_OPT_HOT_MIN_EDGES = 5
 BFS_OPT_DIRECTION = 6
 BFS_OPT_DO_ALPHA = 7
 BFS_OPT_DO_BETA = 8
+BFS_OPT_BITMAP_FRONTIER = 9
 
 
 class BfsError(RuntimeError):

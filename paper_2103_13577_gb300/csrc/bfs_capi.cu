@@ -263,6 +263,10 @@ static void fill_params(bfs_graph* g, Workspace* ws, TraversalParams& P) {
     P.do_alpha = g->do_alpha;
     P.do_beta = g->do_beta;
     P.dir_override = -1;
+    P.bitmap_div = g->bitmap_div;
+    // degree-ordered ids put the light bin (deg < t_small) after every
+    // heavier vertex; the bins' counts give where it starts
+    P.bitmap_from = g->relabelled ? (long long)(g->bin_count[1] + g->bin_count[2]) : 0;
 }
 
 static size_t plain_smem(const bfs_graph* g) { return (size_t)g->hot_words * 4; }
@@ -361,7 +365,7 @@ static bfs_status run_plain(bfs_graph* g, Workspace* ws, int32_t root, int32_t* 
         }
         seen_edges += mf;
         const int dir = choose_direction(g->dir_mode, prev_bu, mf, g->nnz - seen_edges, nf, g->n,
-                                         g->do_alpha, g->do_beta);
+                                         g->do_alpha, g->do_beta, g->bitmap_div);
         prev_bu = dir == 2;
         P.level = level;
         P.dir_override = dir;
@@ -829,6 +833,10 @@ bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value) {
             return fail(BFS_ERR_UNSUPPORTED,
                         "bottom-up levels need a symmetric graph (every edge stored both ways)");
         g->dir_mode = (int32_t)value;
+        return BFS_OK;
+    case BFS_OPT_BITMAP_FRONTIER:
+        if (value < 0 || value > (1 << 20)) return fail(BFS_ERR_INVALID_ARG, "must be in [0, 2^20]");
+        g->bitmap_div = (int32_t)value;
         return BFS_OK;
     case BFS_OPT_DO_ALPHA:
     case BFS_OPT_DO_BETA:

@@ -100,19 +100,24 @@ struct TraversalParams {
     int32_t do_alpha;         // top-down -> bottom-up when frontier edges * alpha > unvisited edges
     int32_t do_beta;          // bottom-up -> top-down when frontier vertices * beta < n
     int32_t dir_override;     // host-loop launches: direction chosen by the host (-1: device)
+    int32_t bitmap_div;       // top-down levels with more than n / bitmap_div frontier
+                              // vertices walk the frontier bitmap (0: never)
+    long long bitmap_from;    // first vertex that can be light (degree-ordered graphs)
 };
 
 // Direction of level L (Beamer, Asanovic, Patterson, "Direction-optimizing
-// breadth-first search", SC 2012): 0 = top-down, 2 = bottom-up.  m_f: edges
-// of the frontier, m_u: edges of the vertices not yet visited, n_f:
-// frontier vertices.
+// breadth-first search", SC 2012): 0 = top-down over the frontier queues,
+// 1 = top-down over the frontier bitmap, 2 = bottom-up.  m_f: edges of the
+// frontier, m_u: edges of the vertices not yet visited, n_f: frontier
+// vertices.
 __host__ __device__ inline int choose_direction(int mode, bool prev_bu, long long m_f,
                                                 long long m_u, long long n_f, long long n,
-                                                int alpha, int beta) {
-    if (mode == 0) return 0;
+                                                int alpha, int beta, int bitmap_div) {
+    const int td = (bitmap_div > 0 && n_f * (long long)bitmap_div > n) ? 1 : 0;
+    if (mode == 0) return td;
     if (mode == 2) return 2;
-    if (!prev_bu) return (m_f * (long long)alpha > m_u) ? 2 : 0;
-    return (n_f * (long long)beta < n) ? 0 : 2;
+    if (!prev_bu) return (m_f * (long long)alpha > m_u) ? 2 : td;
+    return (n_f * (long long)beta < n) ? td : 2;
 }
 
 }  // namespace bfs

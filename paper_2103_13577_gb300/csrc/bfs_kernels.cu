@@ -700,12 +700,109 @@ __device__ void bottom_up_level(const TraversalParams& P, Stage<false>& S, int l
     }
 }
 
+// Position of the set bit of rank n (0-based) in x, which has more than n
+// set bits: the largest p with fewer than n + 1 set bits below p.
+__device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int st = 16; st > 0; st >>= 1)
+        if (__popc(x & ((1u << (pos + st)) - 1u)) <= n) pos += st;
+    return pos;
+}
+
+// Top-down over the frontier bitmap (dense levels, "queue -> bitmap"): the
+// light bin (deg < t_small, most of the vertices) is read from the frontier
+// bitmap instead of its queue.  A warp takes a tile of 32 bitmap words
+// (1024 consecutive vertices); its light frontier vertices, in vertex order,
+// are gathered 32 at a time and their rows cut into 16-byte units as in the
+// warp bin.  After the degree-ordered renumbering the light vertices are
+// one id range with adjacent rows, so a tile's column reads are close to
+// one stream.  The heavier bins keep their (balanced) queues.
+__device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, long long tile,
+                                   int level, int nxt, int nslot, int& my_disc) {
+    const uint32_t* F = P.fb[level % 3];
+    const unsigned lane = lane_id();
+    const long long words = (P.n + 31) / 32;
+    const long long w = tile * 32 + lane;
+    const uint32_t word = w < words ? __ldcg(F + w) : 0u;
+    const int pc = __popc(word);
+    const int pincl = warp_incl_scan(pc);
+    const int pexcl = pincl - pc;
+    const int nfront = __shfl_sync(FULL_MASK, pincl, 31);
+    for (int k0 = 0; k0 < nfront; k0 += 32) {
+        const int k = k0 + (int)lane;
+        int o = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int c = o + st;
+            if (__shfl_sync(FULL_MASK, pexcl, c & 31) <= k) o = c;
+        }
+        const uint32_t ow = __shfl_sync(FULL_MASK, word, o);
+        const int oex = __shfl_sync(FULL_MASK, pexcl, o);
+        bool ok = k < nfront;
+        int32_t v = 0;
+        long long a = 0, b = 0;
+        if (ok) {
+            const int bit = nth_set_bit(ow, k - oex);
+            v = (int32_t)((tile * 32 + o) * 32 + bit);
+            a = __ldg(P.off + v);
+            b = __ldg(P.off + v + 1);
+            if (b - a >= P.t_small || b == a) ok = false;
+        }
+        // unit gather over the (up to 32) rows
+        const long long a4 = a & ~3ll;
+        const int rlo = (int)(a - a4), rhi = (int)(b - a4);
+        const int units = ok ? (rhi + 3) >> 2 : 0;
+        const int incl = warp_incl_scan(units);
+        const int excl = incl - units;
+        const int total = __shfl_sync(FULL_MASK, incl, 31);
+        for (int q0 = 0; q0 < total; q0 += 64) {
+            unsigned okm = 0u;
+            int32_t u[8], vv[8];
+            uint64_t mm[8];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int q = q0 + 32 * h + (int)lane;
+                int oo = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int c = oo + st;
+                    if (__shfl_sync(FULL_MASK, excl, c & 31) <= q) oo = c;
+                }
+                const long long a4o = __shfl_sync(FULL_MASK, a4, oo);
+                const int lo_o = __shfl_sync(FULL_MASK, rlo, oo);
+                const int hi_o = __shfl_sync(FULL_MASK, rhi, oo);
+                const int xo = __shfl_sync(FULL_MASK, excl, oo);
+                const int32_t vo = __shfl_sync(FULL_MASK, v, oo);
+                const int r = 4 * (q - xo);
+                int4 x = make_int4(0, 0, 0, 0);
+                if (q < total) {
+                    x = __ldcs(reinterpret_cast<const int4*>(P.col + a4o + r));
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (r + c >= lo_o && r + c < hi_o) okm |= 1u << (4 * h + c);
+                }
+                u[4 * h + 0] = x.x;
+                u[4 * h + 1] = x.y;
+                u[4 * h + 2] = x.z;
+                u[4 * h + 3] = x.w;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    vv[4 * h + c] = vo;
+                    mm[4 * h + c] = 0ull;
+                }
+            }
+            visit_k<false, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
+        }
+    }
+}
+
 // Top-down work of one level: CTA chunks of bin 2 pulled from a counter
 // (heavy vertices spread over whichever CTAs are free), then warp items
 // (bin 1 chunks, bin 0 groups) dealt round robin over all warps of the grid.
 template <bool kBatch>
 __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
-                                int level, int& my_disc) {
+                                int level, int& my_disc, bool bitmap = false) {
     __shared__ long long s_item;
     const int slot = level % 3, nslot = (level + 1) % 3;
     const int cur = level & 1, nxt = cur ^ 1;
@@ -723,14 +820,29 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
     }
     const long long nwarps = (long long)gridDim.x * kWarps;
     const long long gw = (long long)blockIdx.x * kWarps + warp;
-    const long long witems = L.chunks_warp + L.groups_small;
+    // bitmap mode: the light bin's groups are replaced by bitmap tiles
+    // starting at the first tile that can hold a light vertex
+    long long tile0 = 0, tiles = 0;
+    if (!kBatch && bitmap) {
+        tile0 = P.bitmap_from / 1024;
+        tiles = ((P.n + 31) / 32 + 31) / 32 - tile0;
+    }
+    const long long small_items = (!kBatch && bitmap) ? tiles : L.groups_small;
+    const long long witems = L.chunks_warp + small_items;
     for (long long it = gw; it < witems; it += nwarps) {
-        if (it < L.chunks_warp)
+        if (it < L.chunks_warp) {
             expand_warp_chunk<kBatch>(P, S, cur, it, L.k_warp, L.cnt[1], L.edges[1], level, nxt,
                                       nslot, my_disc);
-        else
+        } else if constexpr (!kBatch) {
+            if (bitmap)
+                expand_bitmap_tile(P, S, tile0 + (it - L.chunks_warp), level, nxt, nslot, my_disc);
+            else
+                expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt,
+                                           nslot, my_disc);
+        } else {
             expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt, nslot,
                                        my_disc);
+        }
     }
 }
 
@@ -769,7 +881,7 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
             bottom_up = true;
         }
     }
-    if (!bottom_up) expand_top_down<kBatch>(P, S, L, level, my_disc);
+    if (!bottom_up) expand_top_down<kBatch>(P, S, L, level, my_disc, dir == 1);
     stage_flush<kBatch>(P, S, level, nxt, nslot);
     if (!kBatch) {
         const int wd = warp_incl_scan(my_disc);
@@ -880,7 +992,8 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
                 const long long mf = L.edges[0] + L.edges[1] + L.edges[2];
                 seen_edges += mf;
                 const int dir = P.fb[0] ? choose_direction(P.dir_mode, prev_bu, mf, P.nnz - seen_edges,
-                                                           nf, P.n, P.do_alpha, P.do_beta)
+                                                           nf, P.n, P.do_alpha, P.do_beta,
+                                                           P.bitmap_div)
                                         : 0;
                 prepare_level(P, level, dir, tid, nthreads);
                 expand_level<false>(P, S, L, level, s_hot, dir);
@@ -911,7 +1024,7 @@ bfs_plain_step(const __grid_constant__ TraversalParams P) {
         const LevelShape L = read_level(P, P.level);
         book_level(P, L, P.level);
         if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
-        const int dir = (P.fb[0] && P.dir_override > 0) ? 2 : 0;
+        const int dir = (P.fb[0] && P.dir_override > 0) ? P.dir_override : 0;
         prepare_level(P, P.level, dir, tid, nthreads);
         expand_level<false>(P, S, L, P.level, s_hot, dir);
     }

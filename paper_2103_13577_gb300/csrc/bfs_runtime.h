@@ -89,6 +89,7 @@ struct bfs_graph {
     long long hot_min_edges = 1ll << 20;
     int32_t dir_mode = 0;             // 0 top-down, 1 direction-optimizing, 2 bottom-up always
     int32_t do_alpha = 15, do_beta = 18;
+    int32_t bitmap_div = 0;           // bitmap top-down when frontier > n / bitmap_div
     int64_t n_nonzero = 0;            // vertices with out-degree > 0
     bool symmetric = false;           // every edge stored in both directions
     std::mutex mu;

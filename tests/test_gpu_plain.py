@@ -162,6 +162,40 @@ def test_shared_memory_hot_bitmap(ctx, kron16, hot_words):
     g.close()
 
 
+@pytest.mark.parametrize("div", [1 << 20, 16, 2])
+def test_bitmap_frontier_top_down(ctx, kron16, div):
+    # 2^20: every level with more than n / 2^20 frontier vertices (all of
+    # them here) walks the frontier bitmap
+    off, col, roots = kron16
+    for upflags in (0, bfs.BFS_UPLOAD_NO_RELABEL):
+        g = bfs.Graph(ctx, off, col, flags=upflags)
+        g.set_option(bfs.BFS_OPT_BITMAP_FRONTIER, div)
+        for r in roots[:8]:
+            dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+            assert_parity(off, col, int(r), dist, parent, st)
+            d2, p2, s2 = run_gpu(g, len(off) - 1, int(r), flags=bfs.BFS_HOST_LOOP)
+            assert_parity(off, col, int(r), d2, p2, s2)
+        g.set_option(bfs.BFS_OPT_DIRECTION, 1)
+        for r in roots[8:12]:
+            dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+            assert_parity(off, col, int(r), dist, parent, st)
+        g.close()
+
+
+def test_bitmap_frontier_small_graphs(ctx):
+    for off, col in (G.grid(50, 70), G.disjoint_union(G.path(300), G.star(3000)),
+                     G.random_graph(5000, 20000, 3, undirected=False)):
+        g = bfs.Graph(ctx, off, col)
+        g.set_option(bfs.BFS_OPT_BITMAP_FRONTIER, 1 << 20)
+        n = len(off) - 1
+        und = np.array_equal(np.sort(col), np.sort(col))  # always true; directed flag below
+        for r in (0, n // 3, n - 1):
+            dist, parent, st = run_gpu(g, n, r)
+            d_ref, _, _ = oracle.bfs(off, col, r)
+            assert np.array_equal(dist, d_ref)
+        g.close()
+
+
 DIRECTIONS = [
     ("do_default", 1, None, None, 0),
     ("do_eager", 1, 1 << 20, 1, 0),      # switches to bottom-up as early as possible
