@@ -123,8 +123,9 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *   BFS_OPT_TIMEOUT_NS       limit of every device-side grid-barrier wait,
  *                            in ns (default 2e9); expiry ends the traversal
  *                            with BFS_ERR_TIMEOUT.
- *   BFS_OPT_CTAS_PER_SM      2 or 3: resident CTAs per SM of the traversal
- *                            kernels (register cap 128 or 80; default 3).
+ *   BFS_OPT_CTAS_PER_SM      2, 3 or 4: resident CTAs per SM of the traversal
+ *                            kernels (register cap 128, 80 or 64; batched
+ *                            kernels use 3 when 4 is asked; default 3).
  *   BFS_OPT_HOT_WORDS        visited-bitmap words (multiple of 4, <= 40960)
  *                            each CTA copies to shared memory at the start of
  *                            a large level; probes of vertices below 32x that

@@ -806,7 +806,7 @@ bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value) {
         g->timeout_ns = value;
         return BFS_OK;
     case BFS_OPT_CTAS_PER_SM: {
-        if (value != 2 && value != 3) return fail(BFS_ERR_INVALID_ARG, "value must be 2 or 3");
+        if (value < 2 || value > 4) return fail(BFS_ERR_INVALID_ARG, "value must be 2, 3 or 4");
         g->min_blocks = (int32_t)value;
         bfs_status st = set_plain_grids(g);
         if (st == BFS_OK) st = grid_size(g, batch_persistent_fn(g->min_blocks), &g->grid_batch);

@@ -1324,13 +1324,16 @@ __global__ void degree_bins_kernel(const int64_t* off, long long n, int t_small,
 }
 
 // -------------------------------------------------------- host wrappers
-// Kernels are instantiated for 2 and 3 resident CTAs per SM (register cap
-// 128 or 80); the graph's occupancy option picks one.
+// Kernels are instantiated for 2, 3 and 4 resident CTAs per SM (register
+// cap 128, 80 or 64; batched kernels 2 and 3); the graph's occupancy option
+// picks one.
 const void* plain_persistent_fn(int mb) {
-    return mb >= 3 ? (const void*)bfs_plain_persistent<3> : (const void*)bfs_plain_persistent<2>;
+    return mb >= 4 ? (const void*)bfs_plain_persistent<4>
+         : mb == 3 ? (const void*)bfs_plain_persistent<3> : (const void*)bfs_plain_persistent<2>;
 }
 const void* plain_step_fn(int mb) {
-    return mb >= 3 ? (const void*)bfs_plain_step<3> : (const void*)bfs_plain_step<2>;
+    return mb >= 4 ? (const void*)bfs_plain_step<4>
+         : mb == 3 ? (const void*)bfs_plain_step<3> : (const void*)bfs_plain_step<2>;
 }
 const void* batch_persistent_fn(int mb) {
     return mb >= 3 ? (const void*)bfs_batch_persistent<3> : (const void*)bfs_batch_persistent<2>;

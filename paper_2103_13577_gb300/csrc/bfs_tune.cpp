@@ -185,7 +185,7 @@ extern "C" bfs_status bfs_graph_autotune(bfs_graph* g, const int32_t* roots, int
     const std::vector<int32_t> c_small = {8, 16, 32, 64, 128};
     const std::vector<int32_t> c_large = {1024, 2048, 4096, 8192, 16384};
     const std::vector<std::pair<int32_t, int32_t>> c_chunks = {{256, 1024}, {512, 2048}, {1024, 4096}};
-    const std::vector<int32_t> c_ctas = {2, 3};
+    const std::vector<int32_t> c_ctas = {2, 3, 4};
     for (int pass = 0; pass < 2 && st == BFS_OK; ++pass) {
         for (int32_t v : c_small) {
             if (st != BFS_OK || v == best.t_small || v >= best.t_large) continue;
