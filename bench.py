@@ -497,6 +497,7 @@ def serve_arm(args):
     for sc in scales:
         off, col = graphgen.kronecker(sc, 16, seed=100 + sc)
         g = bfs.Graph(ctx, off, col)
+        g.set_option(bfs.BFS_OPT_DIRECTION, 1)
         pool_roots = graphgen.pick_roots(off, 256, seed=200 + sc)
         graphs.append({"scale": sc, "n": len(off) - 1, "g": g, "roots": pool_roots,
                        "off": off, "col": col})

@@ -227,13 +227,16 @@ bfs_status bfs_batch_sync(bfs_graph* g, void* stream, bfs_run_stats* stats);
 /* ---- serving ---------------------------------------------------------------
  * A server keeps graphs resident and runs single-root queries as they
  * arrive.  Queries on the same graph that are waiting together are packed
- * into one batched launch of up to 64 lanes; launches run on num_streams
- * CUDA streams so work from different graphs overlaps on the device.  A
- * launch is admitted only while the device memory of all launches in
- * flight stays within memory_budget bytes; queries that do not fit wait.
- * A query whose smallest launch alone exceeds the budget fails with
- * BFS_ERR_BUDGET.  dist_out (host, int32[n]) is written when the query
- * completes; the pointer must stay valid until then. */
+ * into one batched launch of up to 64 lanes; when only a few wait, they run
+ * as that many single-source traversals instead (bfs_server_add_graph times
+ * one of each on the graph to place the cut-over, using the graph's own
+ * options, e.g. BFS_OPT_DIRECTION).  Launches run on num_streams CUDA
+ * streams so work from different graphs overlaps on the device.  A launch is
+ * admitted only while the device memory of all launches in flight stays
+ * within memory_budget bytes; queries that do not fit wait.  A query whose
+ * smallest launch alone exceeds the budget fails with BFS_ERR_BUDGET.
+ * dist_out (host, int32[n]) is written when the query completes; the pointer
+ * must stay valid until then. */
 bfs_status bfs_server_create(bfs_context* ctx, size_t memory_budget, int32_t num_streams,
                              bfs_server** out);
 bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id);

@@ -334,8 +334,8 @@ static bool ctl_empty(const LevelCtl& c) {
            0;
 }
 
-static bfs_status run_plain(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist,
-                            int32_t* parent, cudaStream_t s, uint32_t flags) {
+bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist,
+                        int32_t* parent, cudaStream_t s, uint32_t flags, int32_t grid) {
     TraversalParams P;
     fill_params(g, ws, P);
     P.dist = dist;
@@ -343,7 +343,8 @@ static bfs_status run_plain(bfs_graph* g, Workspace* ws, int32_t root, int32_t* 
     P.root_caller = root;
     const size_t smem = plain_smem(g);
     if (!(flags & BFS_HOST_LOOP))
-        return launch_coop(plain_persistent_fn(g->min_blocks), g->grid_plain, P, s, smem);
+        return launch_coop(plain_persistent_fn(g->min_blocks), grid > 0 ? grid : g->grid_plain, P,
+                           s, smem);
     // host-driven level loop: init, seed, then one launch per level
     bfs_status st;
     const void* fn = plain_step_fn(g->min_blocks);
@@ -437,6 +438,8 @@ bfs_status batch_finish(bfs_graph* g, Workspace* ws, cudaStream_t s, bfs_run_sta
     (void)g;
     return finish(ws, s, stats);
 }
+
+int32_t plain_grid_of(const bfs_graph* g) { return g->grid_plain; }
 
 static bfs_status ensure_workspace(bfs_graph* g, bool batched, cudaStream_t s, Workspace** out) {
     Workspace*& slot = batched ? g->ws_batch : g->ws_plain;
@@ -735,7 +738,7 @@ bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* dist, int32_t* parent, v
         d_dist = ws->dist_scratch;
         d_parent = parent ? ws->parent_scratch : nullptr;
     }
-    if ((st = run_plain(g, ws, root, d_dist, d_parent, s, flags)) != BFS_OK) return st;
+    if ((st = run_plain_on(g, ws, root, d_dist, d_parent, s, flags, 0)) != BFS_OK) return st;
     if (!host) return BFS_OK;
     e = cudaMemcpyAsync(dist, d_dist, g->n * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && parent)

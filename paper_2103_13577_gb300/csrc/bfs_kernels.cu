@@ -134,10 +134,11 @@ __device__ void kernel_exit(const TraversalParams& P) {
 
 // --------------------------------------------------------------- enqueue
 // Claimed vertices are staged per warp in shared memory and appended to the
-// next frontier up to 64 at a time (measured faster than 256 on GB300).  The flush does the per-vertex work that
-// needs random reads (degree from the row offsets, caller numbering) for
-// the whole group at once, writes the distances and parents, bins the
-// group by degree, and reserves queue slots and edge ranges with one 64-bit
+// next frontier up to 64 at a time (measured faster than 256 on GB300).
+// The flush does the per-vertex work that needs random reads (degree from
+// the row offsets, caller numbering) for the whole group at once, writes the
+// distances and parents, bins the group by degree, and reserves queue slots
+// and edge ranges with one 64-bit
 // atomicAdd per bin (the bin counter packs entries << 34 | edge prefix).
 #ifndef BFS_STAGE_CAP
 #define BFS_STAGE_CAP 64

@@ -106,4 +106,7 @@ size_t workspace_bytes(const bfs_graph* g, bool batched, int nlanes);
 bfs_status run_batch_on(bfs_graph* g, Workspace* ws, const int32_t* roots, int32_t k, void* dist,
                         cudaStream_t stream, uint32_t flags, int32_t grid);
 bfs_status batch_finish(bfs_graph* g, Workspace* ws, cudaStream_t stream, bfs_run_stats* stats);
+bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist, int32_t* parent,
+                        cudaStream_t stream, uint32_t flags, int32_t grid);
+int32_t plain_grid_of(const bfs_graph* g);
 }  // namespace bfs

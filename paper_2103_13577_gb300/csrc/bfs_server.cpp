@@ -5,9 +5,11 @@
 // graph.  Whenever a stream slot is free and the server's device arena
 // (its memory budget) can hold a launch's traversal buffers and distance
 // rows, the dispatcher takes up to 64 waiting queries of one graph (graphs
-// served round robin), runs them as one batched traversal on that slot's
-// stream, enqueues the copies of each lane's row into the caller's buffer,
-// and records an event.  Completed events release the memory, which admits
+// served round robin) and runs them on that slot's stream -- as one batched
+// traversal, or, when few are waiting, as that many single-source
+// traversals (the cut-over is calibrated per graph when it is added) --
+// enqueues the copies of each query's row into the caller's buffer, and
+// records an event.  Completed events release the memory, which admits
 // the next launch -- so queries that arrive while others are on the GPU
 // join the next launch on a free slot, and launches on different slots
 // overlap on the device (each launch's persistent grid is sized to a share
@@ -45,10 +47,19 @@ struct Query {
 struct Launch {
     int slot = -1;
     int32_t graph_id = 0;
+    bool plain = false;      // k single-source traversals instead of one batched launch
     Workspace* ws = nullptr;
     void* d_dist = nullptr;
     std::vector<std::shared_ptr<Query>> lanes;
     cudaEvent_t done = nullptr;
+};
+
+// Per-graph launch policy: up to plain_max waiting queries are served as
+// that many single-source traversals (cheaper than one batched launch,
+// whose cost barely depends on how many lanes it carries); more go batched.
+struct GraphPolicy {
+    int32_t plain_max = 0;
+    double plain_ms = 0.0, batch_ms = 0.0;
 };
 
 struct SlotState {
@@ -67,6 +78,7 @@ struct bfs_server {
     void* arena = nullptr;
     DeviceAllocator* mem = nullptr;
     std::vector<bfs_graph*> graphs;
+    std::vector<GraphPolicy> policy;
     std::vector<std::deque<std::shared_ptr<Query>>> pending;
     std::unordered_map<bfs_ticket, std::shared_ptr<Query>> tickets;
     std::vector<SlotState> slots;
@@ -85,7 +97,8 @@ struct bfs_server {
 namespace bfs {
 
 static size_t launch_bytes(const bfs_graph* g, int k) {
-    return workspace_bytes(g, true, k) + 256 * 32 + (size_t)k * g->n * 4 + 4096;
+    return std::min(workspace_bytes(g, true, k), workspace_bytes(g, false, k)) + 256 * 32 +
+           (size_t)k * g->n * 4 + 4096;
 }
 
 // Runs with s->mu held.  Returns true when something was launched.
@@ -104,10 +117,11 @@ static bool try_launch(bfs_server* s) {
         if (q.empty()) continue;
         bfs_graph* g = s->graphs[gid];
         const int k = (int)std::min<size_t>(64, q.size());
+        const bool plain = k <= s->policy[gid].plain_max;
         SlotState& sl = s->slots[free_slot];
         bfs_status st = BFS_OK;
         cudaSetDevice(s->ctx->device);
-        Workspace* ws = make_workspace(g, s->mem, true, sl.stream, &st);
+        Workspace* ws = make_workspace(g, s->mem, !plain, sl.stream, &st);
         void* d_dist = ws ? s->mem->alloc((size_t)k * g->n * 4) : nullptr;
         if (!ws || !d_dist) {
             if (ws) free_workspace(g, ws);
@@ -128,9 +142,18 @@ static bool try_launch(bfs_server* s) {
         }
         // a share of the persistent grid so that launches on other slots
         // can be resident at the same time
-        const int32_t share =
-            std::max<int32_t>(s->ctx->sms, g->grid_batch / (int32_t)s->slots.size());
-        st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, 0, share);
+        L.plain = plain;
+        if (plain) {
+            const int32_t share =
+                std::max<int32_t>(s->ctx->sms, plain_grid_of(g) / (int32_t)s->slots.size());
+            for (int i = 0; i < k && st == BFS_OK; ++i)
+                st = run_plain_on(g, ws, roots[i], static_cast<int32_t*>(d_dist) + (size_t)i * g->n,
+                                  nullptr, sl.stream, 0, share);
+        } else {
+            const int32_t share =
+                std::max<int32_t>(s->ctx->sms, g->grid_batch / (int32_t)s->slots.size());
+            st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, 0, share);
+        }
         if (st == BFS_OK) {
             for (int i = 0; i < k; ++i) {
                 cudaError_t e = cudaMemcpyAsync(L.lanes[i]->dist_out,
@@ -288,8 +311,60 @@ bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id) 
         set_error("null argument");
         return BFS_ERR_INVALID_ARG;
     }
+    // calibrate the launch policy: one single-source run and one 64-lane
+    // batched run of the same root, each timed on a scratch stream
+    GraphPolicy pol;
+    {
+        cudaSetDevice(s->ctx->device);
+        bfs_status st = BFS_OK;
+        Workspace* wp = make_workspace(g, s->ctx->mem, false, nullptr, &st);
+        Workspace* wb = wp ? make_workspace(g, s->ctx->mem, true, nullptr, &st) : nullptr;
+        void* d = wb ? s->ctx->mem->alloc((size_t)64 * g->n * 4) : nullptr;
+        if (!wp || !wb || !d) {
+            if (wp) free_workspace(g, wp);
+            if (wb) free_workspace(g, wb);
+            set_error("server: device memory exhausted while calibrating a graph");
+            return BFS_ERR_NO_MEMORY;
+        }
+        int32_t root = 0;
+        for (; root < g->n; ++root) {  // a vertex with out-edges (first in degree order)
+            int64_t o[2];
+            if (cudaMemcpy(o, g->d_off + root, 16, cudaMemcpyDeviceToHost) != cudaSuccess) break;
+            if (o[1] > o[0]) break;
+        }
+        if (root >= g->n) root = 0;
+        std::vector<int32_t> roots(64, root);
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float tp = 0.f, tb = 0.f;
+        for (int rep = 0; rep < 2 && st == BFS_OK; ++rep) {
+            cudaEventRecord(e0, nullptr);
+            st = run_plain_on(g, wp, root, static_cast<int32_t*>(d), nullptr, nullptr, 0, 0);
+            cudaEventRecord(e1, nullptr);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&tp, e0, e1);
+            if (st != BFS_OK) break;
+            cudaEventRecord(e0, nullptr);
+            st = run_batch_on(g, wb, roots.data(), 64, d, nullptr, 0, 0);
+            cudaEventRecord(e1, nullptr);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&tb, e0, e1);
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cudaDeviceSynchronize();
+        s->ctx->mem->release(d);
+        free_workspace(g, wp);
+        free_workspace(g, wb);
+        if (st != BFS_OK) return st;
+        pol.plain_ms = tp;
+        pol.batch_ms = tb;
+        pol.plain_max = tp > 0.f ? std::min(63, std::max(0, (int)(tb / tp))) : 0;
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     s->graphs.push_back(g);
+    s->policy.push_back(pol);
     s->pending.emplace_back();
     *graph_id = (int32_t)s->graphs.size() - 1;
     return BFS_OK;
