@@ -265,6 +265,39 @@ bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out);
 /* Stops the server; queued queries finish with BFS_ERR_CANCELLED. */
 bfs_status bfs_server_destroy(bfs_server* s);
 
+/* ---- ButterFly BFS emulated on one GPU -----------------------------------------
+ * Algorithm 2 with `nodes` virtual compute nodes on this device: each node
+ * keeps its own distance array, owns one 1D vertex range of about nnz/nodes
+ * adjacency entries (Section "Graph Partitioning"), expands only its owned
+ * frontier (Phase 1, atomic claim per node), then log_r(nodes) butterfly
+ * rounds (Phase 2, r = max(2, fanout)): in round i a node receives the
+ * global queue of every node whose base-r id differs only in digit i,
+ * filters it by its own distances and enqueues the new vertices.  nodes
+ * must be a power of r (1..256), fanout 1..16.  dist: device int32[n] in the
+ * caller's numbering (node 0's view; every node's view is compared and the
+ * differences counted).  Waits for `stream`.  Nodes run one after another:
+ * this is for correctness and the message accounting of Section "Fanout &
+ * Trade-offs" (messages per level = nodes * (r - 1) * rounds; a node's
+ * receive buffer holds at most (r - 1) global queues, O(f * V)), not speed. */
+typedef struct bfs_butterfly_stats {
+    int64_t levels;
+    int64_t rounds_per_level;
+    int64_t messages;                  /* queue transfers between nodes */
+    int64_t message_entries;           /* vertex ids carried by them */
+    int64_t max_round_buffer_entries;  /* largest receive buffer of one node in one round */
+    int64_t max_global_queue;          /* largest Q_global at the start of a round */
+    int64_t node_disagreements;        /* (node, vertex) distances differing from node 0 */
+    int32_t nodes, radix;
+} bfs_butterfly_stats;
+bfs_status bfs_run_butterfly(bfs_graph* g, int32_t root, int32_t nodes, int32_t fanout,
+                             int32_t* dist, void* stream, bfs_butterfly_stats* stats);
+/* The exchange schedule itself (host only, no device work): the nodes whose
+ * global queues `node` receives in round `round` (ButterflyDirection of
+ * Algorithm 2 generalised to fanout f: the ids differing from `node` only in
+ * base-max(2,f) digit `round`).  partners: room for 15 ids; *count set. */
+bfs_status bfs_butterfly_schedule(int32_t nodes, int32_t fanout, int32_t round, int32_t node,
+                                  int32_t* partners, int32_t* count);
+
 /* ---- traversal without device allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory at traversal time -- code that runs inside a

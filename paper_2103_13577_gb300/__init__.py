@@ -47,6 +47,7 @@ from .api import (  # noqa: F401
     Graph,
     Server,
     bfs_batch_sync,
+    bfs_butterfly_schedule,
     bfs_context_create,
     bfs_context_destroy,
     bfs_graph_autotune,
@@ -60,6 +61,7 @@ from .api import (  # noqa: F401
     bfs_release,
     bfs_run,
     bfs_run_batch,
+    bfs_run_butterfly,
     bfs_run_static,
     bfs_server_add_graph,
     bfs_server_create,

@@ -69,6 +69,14 @@ class TuneResult(ctypes.Structure):
                 ("fingerprint", ctypes.c_uint64)]
 
 
+class ButterflyStats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int64), ("rounds_per_level", ctypes.c_int64),
+                ("messages", ctypes.c_int64), ("message_entries", ctypes.c_int64),
+                ("max_round_buffer_entries", ctypes.c_int64), ("max_global_queue", ctypes.c_int64),
+                ("node_disagreements", ctypes.c_int64), ("nodes", ctypes.c_int32),
+                ("radix", ctypes.c_int32)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("launches", ctypes.c_int64),
@@ -95,6 +103,9 @@ SIGNATURES = {
     "bfs_graph_autotune": (_i32, [_vp, _vp, _i32, _u32, ctypes.c_char_p, ctypes.POINTER(TuneResult)]),
     "bfs_graph_sync": (_i32, [_vp, _vp, ctypes.POINTER(RunStats)]),
     "bfs_run_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _u32]),
+    "bfs_run_butterfly": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(ButterflyStats)]),
+    "bfs_butterfly_schedule": (_i32, [_i32, _i32, _i32, _i32, ctypes.POINTER(_i32),
+                                      ctypes.POINTER(_i32)]),
     "bfs_batch_sync": (_i32, [_vp, _vp, ctypes.POINTER(RunStats)]),
     "bfs_server_create": (_i32, [_vp, _sz, _i32, _pp]),
     "bfs_server_add_graph": (_i32, [_vp, _vp, ctypes.POINTER(_i32)]),

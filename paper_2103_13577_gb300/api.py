@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (BFS_DIST_INT8, BFS_OUT_HOST, BFS_TUNE_BATCHED, BFS_UPLOAD_DEVICE_PTRS,
-                   GraphInfo, RunStats, ServerStats, TuneResult, check)
+                   ButterflyStats, GraphInfo, RunStats, ServerStats, TuneResult, check)
 
 
 def _is_torch(x) -> bool:
@@ -150,6 +150,26 @@ def bfs_run_static(row_off, col, root: int, dist, parent=None, stream=None,
     return {f: getattr(st, f) for f, _ in RunStats._fields_} if wait else None
 
 
+def bfs_run_butterfly(g: int, root: int, nodes: int, fanout: int, dist, stream=None) -> dict:
+    """Algorithm 2 emulated with `nodes` virtual compute nodes on this GPU."""
+    p_dist, dev = _buf(dist, np.int32)
+    if not dev:
+        raise ValueError("dist must be a device buffer")
+    st = ButterflyStats()
+    check(_lib.lib().bfs_run_butterfly(g, int(root), nodes, fanout, p_dist, _stream(stream),
+                                       ctypes.byref(st)), "bfs_run_butterfly")
+    return {f: getattr(st, f) for f, _ in ButterflyStats._fields_}
+
+
+def bfs_butterfly_schedule(nodes: int, fanout: int, round_: int, node: int) -> list[int]:
+    """Nodes whose global queues `node` receives in round `round_` (host only)."""
+    buf = (ctypes.c_int32 * 16)()
+    cnt = ctypes.c_int32()
+    check(_lib.lib().bfs_butterfly_schedule(nodes, fanout, round_, node, buf, ctypes.byref(cnt)),
+          "bfs_butterfly_schedule")
+    return [buf[i] for i in range(cnt.value)]
+
+
 def bfs_graph_sync(g: int, stream=None) -> dict:
     st = RunStats()
     check(_lib.lib().bfs_graph_sync(g, _stream(stream), ctypes.byref(st)), "bfs_graph_sync")
@@ -276,6 +296,9 @@ class Graph:
 
     def sync(self, stream=None) -> dict:
         return bfs_graph_sync(self.handle, stream)
+
+    def run_butterfly(self, root, nodes, fanout, dist, stream=None) -> dict:
+        return bfs_run_butterfly(self.handle, root, nodes, fanout, dist, stream)
 
     def run_batch(self, roots, dist, stream=None, flags=0):
         bfs_run_batch(self.handle, roots, dist, stream, flags)
