@@ -322,6 +322,20 @@ def gpu_arm(args, rank, world, local_rank):
         do_ms = t_d.cpu().numpy()
     do_value = hmean(m_job / (do_ms * 1e-3) / 1e9)
 
+    # the paper's own scheme (per-level LRB binning, one kernel per bin on its
+    # own stream, host-driven levels) on the same roots, for comparison
+    lrb_ms = np.zeros(NROOTS)
+    for r in roots[:2]:
+        g.run_lrb(int(r), dist, stream=stream)
+    lev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for i, r in enumerate(roots):
+        lev[0].record(stream)
+        g.run_lrb(int(r), dist, stream=stream)
+        lev[1].record(stream)
+        torch.cuda.synchronize(dev_)
+        lrb_ms[i] = lev[0].elapsed_time(lev[1])
+    lrb_value = hmean(m_c / (lrb_ms * 1e-3) / 1e9)
+
     # 64-root batched launch on the same graph (one persistent launch)
     bd = torch.empty((NROOTS, n), dtype=torch.int32, device=dev_)
     for _ in range(2):
@@ -381,6 +395,10 @@ def gpu_arm(args, rank, world, local_rank):
                 "bottom_up_levels_last_root": int(do_st["bottom_up_levels"]),
                 "note": "BFS_OPT_DIRECTION=1; GTEPS counts m_c (the top-down edge work), "
                         "bottom-up levels examine fewer edges"},
+            "paper_lrb_scheme": {
+                "value": lrb_value, "unit": "GTEPS", "root_ms_median": float(np.median(lrb_ms)),
+                "note": "per-level log2-degree binning, one kernel per bin on its own stream, "
+                        "host-driven level loop (bfs_run_lrb), same roots, this rank"},
             "batched": {"roots": NROOTS, "ms": batch_ms, "gteps": batch_gteps,
                         "edges": int(bst["edges_scanned"]), "levels": int(bst["levels"]),
                         "speedup_vs_plain_step": ms_step / batch_ms},

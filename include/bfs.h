@@ -298,6 +298,23 @@ bfs_status bfs_run_butterfly(bfs_graph* g, int32_t root, int32_t nodes, int32_t 
 bfs_status bfs_butterfly_schedule(int32_t nodes, int32_t fanout, int32_t round, int32_t node,
                                   int32_t* partners, int32_t* count);
 
+/* ---- the paper's load-balancing scheme, for comparison ---------------------------
+ * Single-source traversal run the way Section "Load Balanced Traversals Per
+ * compute-node" describes: each level the frontier is grouped by Logarithmic
+ * Radix Binning (bin b: degrees in [2^(b-1), 2^b)), one kernel per non-empty
+ * bin is launched on its own stream with a thread-block shape taken from the
+ * bin's degree bound (thread, warp or block per vertex), the host joins the
+ * streams and reads the next frontier size.  Visited test: d[u] = infinity
+ * claimed by compare-and-swap.  dist: device int32[n], caller numbering.
+ * Waits for `stream`.  An ablation against bfs_run's fused persistent
+ * design, not a faster path. */
+typedef struct bfs_lrb_stats {
+    int64_t levels;
+    int64_t kernels;   /* bin kernels launched */
+} bfs_lrb_stats;
+bfs_status bfs_run_lrb(bfs_graph* g, int32_t root, int32_t* dist, void* stream,
+                       bfs_lrb_stats* stats);
+
 /* ---- traversal without device allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory at traversal time -- code that runs inside a

@@ -62,6 +62,7 @@ from .api import (  # noqa: F401
     bfs_run,
     bfs_run_batch,
     bfs_run_butterfly,
+    bfs_run_lrb,
     bfs_run_static,
     bfs_server_add_graph,
     bfs_server_create,

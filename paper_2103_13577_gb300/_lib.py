@@ -77,6 +77,10 @@ class ButterflyStats(ctypes.Structure):
                 ("radix", ctypes.c_int32)]
 
 
+class LrbStats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int64), ("kernels", ctypes.c_int64)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("launches", ctypes.c_int64),
@@ -104,6 +108,7 @@ SIGNATURES = {
     "bfs_graph_sync": (_i32, [_vp, _vp, ctypes.POINTER(RunStats)]),
     "bfs_run_batch": (_i32, [_vp, _vp, _i32, _vp, _vp, _u32]),
     "bfs_run_butterfly": (_i32, [_vp, _i32, _i32, _i32, _vp, _vp, ctypes.POINTER(ButterflyStats)]),
+    "bfs_run_lrb": (_i32, [_vp, _i32, _vp, _vp, ctypes.POINTER(LrbStats)]),
     "bfs_butterfly_schedule": (_i32, [_i32, _i32, _i32, _i32, ctypes.POINTER(_i32),
                                       ctypes.POINTER(_i32)]),
     "bfs_batch_sync": (_i32, [_vp, _vp, ctypes.POINTER(RunStats)]),

@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (BFS_DIST_INT8, BFS_OUT_HOST, BFS_TUNE_BATCHED, BFS_UPLOAD_DEVICE_PTRS,
-                   ButterflyStats, GraphInfo, RunStats, ServerStats, TuneResult, check)
+                   ButterflyStats, GraphInfo, LrbStats, RunStats, ServerStats, TuneResult, check)
 
 
 def _is_torch(x) -> bool:
@@ -161,6 +161,17 @@ def bfs_run_butterfly(g: int, root: int, nodes: int, fanout: int, dist, stream=N
     return {f: getattr(st, f) for f, _ in ButterflyStats._fields_}
 
 
+def bfs_run_lrb(g: int, root: int, dist, stream=None) -> dict:
+    """The paper's per-bin-kernel traversal (comparison path)."""
+    p_dist, dev = _buf(dist, np.int32)
+    if not dev:
+        raise ValueError("dist must be a device buffer")
+    st = LrbStats()
+    check(_lib.lib().bfs_run_lrb(g, int(root), p_dist, _stream(stream), ctypes.byref(st)),
+          "bfs_run_lrb")
+    return {f: getattr(st, f) for f, _ in LrbStats._fields_}
+
+
 def bfs_butterfly_schedule(nodes: int, fanout: int, round_: int, node: int) -> list[int]:
     """Nodes whose global queues `node` receives in round `round_` (host only)."""
     buf = (ctypes.c_int32 * 16)()
@@ -296,6 +307,9 @@ class Graph:
 
     def sync(self, stream=None) -> dict:
         return bfs_graph_sync(self.handle, stream)
+
+    def run_lrb(self, root, dist, stream=None) -> dict:
+        return bfs_run_lrb(self.handle, root, dist, stream)
 
     def run_butterfly(self, root, nodes, fanout, dist, stream=None) -> dict:
         return bfs_run_butterfly(self.handle, root, nodes, fanout, dist, stream)

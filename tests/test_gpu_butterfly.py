@@ -75,3 +75,28 @@ def test_butterfly_rejects_bad_node_counts(ctx):
         with pytest.raises(bfs.BfsError):
             g.run_butterfly(0, nodes, fanout, d)
     g.close()
+
+
+@pytest.mark.parametrize("graph", ["kron14", "path", "union", "er", "directed"])
+def test_lrb_comparison_path_matches_oracle(ctx, graph):
+    flags = 0
+    if graph == "kron14":
+        off, col = graphgen.kronecker(14, 16, seed=32)
+    elif graph == "path":
+        off, col = G.path(400)
+    elif graph == "union":
+        off, col = G.disjoint_union(G.grid(30, 40), G.star(3000))
+    elif graph == "er":
+        off, col = graphgen.erdos_renyi(13, 16, seed=33)
+        flags = bfs.BFS_UPLOAD_NO_RELABEL
+    else:
+        off, col = G.random_graph(3000, 12000, 4, undirected=False)
+    n = len(off) - 1
+    g = bfs.Graph(ctx, off, col, flags=flags)
+    for r in (0, n // 2, n - 1):
+        dist = torch.empty(n, dtype=torch.int32, device="cuda")
+        st = g.run_lrb(r, dist)
+        ref, _, info = oracle.bfs(off, col, r)
+        assert np.array_equal(dist.cpu().numpy(), ref)
+        assert st["levels"] == info["levels"] and st["kernels"] >= st["levels"] - 1
+    g.close()
