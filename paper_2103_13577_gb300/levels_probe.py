@@ -2,7 +2,9 @@
 16) and runs two single-source traversals with BFS_HOST_LOOP, so that each
 BFS level is its own kernel launch (one ncu result per level).
 
-  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent]
+  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent|do]
+
+do: host-loop launches with the direction-optimizing mode.
 """
 from __future__ import annotations
 
@@ -27,7 +29,9 @@ def main():
     n = len(off) - 1
     dist = torch.empty(n, dtype=torch.int32, device="cuda")
     par = torch.empty(n, dtype=torch.int32, device="cuda")
-    flags = bfs.BFS_HOST_LOOP if mode == "hostloop" else 0
+    flags = bfs.BFS_HOST_LOOP if mode in ("hostloop", "do") else 0
+    if mode == "do":
+        g.set_option(bfs.BFS_OPT_DIRECTION, 1)
     for r in roots[:2]:
         g.run(int(r), dist, par, flags=flags)
         print(g.sync(), flush=True)
