@@ -110,8 +110,9 @@ typedef struct bfs_graph_info {
 bfs_status bfs_graph_get_info(const bfs_graph* g, bfs_graph_info* out);
 
 /* Degree-bin thresholds and base chunk sizes (the autotuner's knobs).
- * t_small >= 1, t_large > t_small, chunk_warp a multiple of 128,
- * chunk_cta a multiple of 1024.  Defaults 32, 4096, 512, 2048.  Reallocates the per-traversal buffers;
+ * t_small >= 1, t_large > t_small, chunk_warp a power of two in
+ * [128, 2^24], chunk_cta a power of two in [1024, 2^24] (chunk starts are
+ * found with shifts).  Defaults 32, 4096, 512, 2048.  Reallocates the per-traversal buffers;
  * must not be called while a traversal on g is in flight. */
 bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
                               int32_t chunk_warp, int32_t chunk_cta);
@@ -151,7 +152,13 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *                            t_small) from the frontier bitmap in vertex order
  *                            (tiles of 1024 vertices per warp) instead of that
  *                            bin's queue; the heavier bins keep their queues.
- *                            0: never (default). */
+ *                            0: never (default).
+ *   BFS_OPT_L2_PREFETCH      0/1: when a warp (bin 1) or CTA (bin 2) takes its
+ *                            next batch of vertices, one bulk L2 prefetch per
+ *                            vertex requests that vertex's column segment
+ *                            (bin 2: its first 32 KiB, the rest 32 KiB ahead
+ *                            of the reads), so the segment's reads find it in
+ *                            L2 instead of each waiting on HBM.  Default 0. */
 #define BFS_OPT_WARP_AGGREGATE  1
 #define BFS_OPT_TIMEOUT_NS      2
 #define BFS_OPT_CTAS_PER_SM     3
@@ -161,6 +168,7 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
 #define BFS_OPT_DO_ALPHA        7
 #define BFS_OPT_DO_BETA         8
 #define BFS_OPT_BITMAP_FRONTIER 9
+#define BFS_OPT_L2_PREFETCH     10
 bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value);
 
 /* ---- autotuning -----------------------------------------------------------------
@@ -360,6 +368,16 @@ int32_t bfs_version(void);
  * kernel returns normally; the context stays usable.  timeout_ns = 0
  * restores normal operation (default limit). */
 bfs_status bfs_debug_set_barrier_test(bfs_graph* g, int32_t stall, int64_t timeout_ns);
+
+/* Level timeline of the persistent single-source traversal (bfs_run without
+ * BFS_HOST_LOOP).  d_stamps: device array of cap >= 3 uint64 entries, owned
+ * by the caller and kept alive while traversals run; nullptr turns the
+ * timeline off (default).  Each traversal writes %globaltimer (ns) into
+ * d_stamps[0] at kernel start, [1] after the initialisation barrier, [2]
+ * after the root is seeded and [3 + L] after level L's barrier, for as many
+ * levels as fit; entries past the last level are left unwritten.  The
+ * timestamps cost one store per level. */
+bfs_status bfs_debug_set_timeline(bfs_graph* g, uint64_t* d_stamps, int32_t cap);
 
 #ifdef __cplusplus
 }

@@ -30,6 +30,7 @@ from ._lib import (  # noqa: F401
     BFS_OPT_DO_BETA,
     BFS_OPT_HOT_MIN_EDGES,
     BFS_OPT_HOT_WORDS,
+    BFS_OPT_L2_PREFETCH,
     BFS_OPT_TIMEOUT_NS,
     BFS_OPT_WARP_AGGREGATE,
     BFS_OK,
@@ -50,6 +51,7 @@ from .api import (  # noqa: F401
     bfs_butterfly_schedule,
     bfs_context_create,
     bfs_context_destroy,
+    bfs_debug_set_timeline,
     bfs_graph_autotune,
     bfs_graph_free,
     bfs_graph_get_info,

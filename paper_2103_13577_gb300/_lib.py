@@ -39,6 +39,7 @@ BFS_OPT_DIRECTION = 6
 BFS_OPT_DO_ALPHA = 7
 BFS_OPT_DO_BETA = 8
 BFS_OPT_BITMAP_FRONTIER = 9
+BFS_OPT_L2_PREFETCH = 10
 
 
 class BfsError(RuntimeError):
@@ -126,6 +127,7 @@ SIGNATURES = {
     "bfs_status_string": (ctypes.c_char_p, [_i32]),
     "bfs_version": (_i32, []),
     "bfs_debug_set_barrier_test": (_i32, [_vp, _i32, _i64]),
+    "bfs_debug_set_timeline": (_i32, [_vp, _vp, _i32]),
     "bfs_run_static": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _vp, _vp, ctypes.POINTER(RunStats)]),
 }
 

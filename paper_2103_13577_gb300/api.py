@@ -181,6 +181,19 @@ def bfs_butterfly_schedule(nodes: int, fanout: int, round_: int, node: int) -> l
     return [buf[i] for i in range(cnt.value)]
 
 
+def bfs_debug_set_timeline(g: int, stamps) -> None:
+    """Attach a device int64 tensor (>= 3 entries) that every persistent
+    single-source traversal fills with %globaltimer stamps: [0] start, [1]
+    after init, [2] after the seed, [3 + L] after level L.  None detaches."""
+    if stamps is None:
+        check(_lib.lib().bfs_debug_set_timeline(g, None, 0), "bfs_debug_set_timeline")
+        return
+    p, dev = _buf(stamps, np.int64)
+    if not dev:
+        raise ValueError("the timeline must be a device tensor")
+    check(_lib.lib().bfs_debug_set_timeline(g, p, int(stamps.numel())), "bfs_debug_set_timeline")
+
+
 def bfs_graph_sync(g: int, stream=None) -> dict:
     st = RunStats()
     check(_lib.lib().bfs_graph_sync(g, _stream(stream), ctypes.byref(st)), "bfs_graph_sync")

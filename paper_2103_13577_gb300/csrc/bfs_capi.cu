@@ -267,6 +267,9 @@ static void fill_params(bfs_graph* g, Workspace* ws, TraversalParams& P) {
     // degree-ordered ids put the light bin (deg < t_small) after every
     // heavier vertex; the bins' counts give where it starts
     P.bitmap_from = g->relabelled ? (long long)(g->bin_count[1] + g->bin_count[2]) : 0;
+    P.l2_prefetch = g->l2_prefetch;
+    P.timeline = reinterpret_cast<unsigned long long*>(g->timeline);
+    P.timeline_cap = g->timeline ? g->timeline_cap : 0;
 }
 
 static size_t plain_smem(const bfs_graph* g) { return (size_t)g->hot_words * 4; }
@@ -692,9 +695,13 @@ bfs_status bfs_graph_get_info(const bfs_graph* g, bfs_graph_info* out) {
 bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large, int32_t chunk_warp,
                               int32_t chunk_cta) {
     if (!g) return fail(BFS_ERR_INVALID_ARG, "null graph");
+    auto pow2 = [](int32_t x) { return x > 0 && (x & (x - 1)) == 0; };
     if (t_small < 1 || t_large <= t_small || t_small > (1 << 20) || chunk_warp < 128 ||
-        chunk_warp % 128 || chunk_cta < 1024 || chunk_cta % 1024)
-        return fail(BFS_ERR_INVALID_ARG, "bad bin thresholds or chunk sizes");
+        chunk_warp > (1 << 24) || !pow2(chunk_warp) || chunk_cta < 1024 ||
+        chunk_cta > (1 << 24) || !pow2(chunk_cta))
+        return fail(BFS_ERR_INVALID_ARG,
+                    "bad bin thresholds or chunk sizes (chunks: powers of two, warp >= 128, "
+                    "CTA >= 1024, both <= 2^24)");
     std::lock_guard<std::mutex> lk(g->mu);
     cudaSetDevice(g->ctx->device);
     cudaError_t e = cudaDeviceSynchronize();
@@ -837,6 +844,10 @@ bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value) {
                         "bottom-up levels need a symmetric graph (every edge stored both ways)");
         g->dir_mode = (int32_t)value;
         return BFS_OK;
+    case BFS_OPT_L2_PREFETCH:
+        if (value < 0 || value > 1) return fail(BFS_ERR_INVALID_ARG, "must be 0 or 1");
+        g->l2_prefetch = (int32_t)value;
+        return BFS_OK;
     case BFS_OPT_BITMAP_FRONTIER:
         if (value < 0 || value > (1 << 20)) return fail(BFS_ERR_INVALID_ARG, "must be in [0, 2^20]");
         g->bitmap_div = (int32_t)value;
@@ -855,6 +866,15 @@ bfs_status bfs_debug_set_barrier_test(bfs_graph* g, int32_t stall, int64_t timeo
     std::lock_guard<std::mutex> lk(g->mu);
     g->debug_stall = stall ? 1 : 0;
     g->timeout_ns = timeout_ns > 0 ? timeout_ns : 2000000000ll;
+    return BFS_OK;
+}
+
+bfs_status bfs_debug_set_timeline(bfs_graph* g, uint64_t* d_stamps, int32_t cap) {
+    if (!g) return fail(BFS_ERR_INVALID_ARG, "null graph");
+    if (d_stamps && cap < 3) return fail(BFS_ERR_INVALID_ARG, "a timeline needs at least 3 entries");
+    std::lock_guard<std::mutex> lk(g->mu);
+    g->timeline = d_stamps;
+    g->timeline_cap = d_stamps ? cap : 0;
     return BFS_OK;
 }
 

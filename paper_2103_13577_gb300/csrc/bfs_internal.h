@@ -103,6 +103,9 @@ struct TraversalParams {
     int32_t bitmap_div;       // top-down levels with more than n / bitmap_div frontier
                               // vertices walk the frontier bitmap (0: never)
     long long bitmap_from;    // first vertex that can be light (degree-ordered graphs)
+    int32_t l2_prefetch;      // bulk L2 prefetch of the heavy bins' column segments
+    int32_t timeline_cap;     // entries of timeline
+    unsigned long long* timeline;  // nullable: %globaltimer after init, seed and each level
 };
 
 // Direction of level L (Beamer, Asanovic, Patterson, "Direction-optimizing

@@ -75,6 +75,27 @@ __device__ __forceinline__ void raise_status(const TraversalParams& P, int code)
     atomicCAS(&P.stats->status, 0, code);
 }
 
+// One bulk request that brings col[a, b) into L2 (cp.async.bulk.prefetch:
+// no shared memory, no completion to wait for).  Start and size must be
+// multiples of 16 bytes; col is padded past its last entry, so rounding the
+// end up stays inside the allocation.
+__device__ __forceinline__ void prefetch_cols_l2(const int32_t* col, long long a, long long b) {
+    if (b <= a) return;
+    const long long a4 = a & ~3ll, b4 = (b + 3) & ~3ll;
+    const unsigned bytes = (unsigned)((b4 - a4) * 4);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(col + a4), "r"(bytes)
+                 : "memory");
+}
+
+// Prefetch distance of the heavy bins, in column entries (32 KiB).
+constexpr long long kPrefetchAhead = 8192;
+
+// Level timeline (diagnostics): block 0, thread 0 records %globaltimer.
+__device__ __forceinline__ void stamp(const TraversalParams& P, int i) {
+    if (P.timeline && i < P.timeline_cap && blockIdx.x == 0 && threadIdx.x == 0)
+        P.timeline[i] = global_timer_ns();
+}
+
 // ------------------------------------------------------------ grid barrier
 // All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA
 // arrives on a counter; the last arrival resets it and bumps a generation
@@ -157,10 +178,17 @@ struct Stage {
 };
 
 // Warp-collective flush of the staged entries into the next frontier.
-// Lane l owns entries [8 l, 8 l + 8): all their random reads (row offsets,
-// caller numbering) are issued together; per bin one warp scan of
-// (entries, degree sum) and one packed atomicAdd place the lane's entries
-// at consecutive queue slots.
+// Lane l owns entries [H l, H l + H): all their random reads (row offsets,
+// caller numbering) are issued together; one packed atomicAdd per bin,
+// issued by lanes 0..2 at once, places the lane's entries at consecutive
+// queue slots.
+//
+// The function is out of line (it is called from many places), so P
+// arrives as a generic pointer into the launch parameters.  Fields are read
+// into registers before the stores that follow them: a read after a store
+// through a generic pointer cannot be moved above it (the compiler cannot
+// rule out that the store changed the parameter), and re-reads inside the
+// store loops would put a round trip on every iteration.
 template <bool kBatch>
 __device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>& S, int level,
                                          int nxt, int nslot) {
@@ -168,6 +196,16 @@ __device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>
     const unsigned lane = lane_id();
     const int n = S.cnt;
     if (n == 0) return;
+    const int64_t* const off = P.off;
+    const int32_t* const new2old = P.new2old;
+    int32_t* const dist = P.dist;
+    int32_t* const parent = P.parent;
+    uint32_t* const fbn = P.fb[0] ? P.fb[(level + 1) % 3] : nullptr;
+    const int t_small = P.t_small, t_large = P.t_large;
+    const int sh_warp = __ffs(P.chunk_warp) - 1, sh_cta = __ffs(P.chunk_cta) - 1;
+    unsigned long long* const packed = P.ctl[nslot].packed;
+    bool overflow = false;
+
     const int i0 = (int)lane * H;
     int32_t u[H];
     int deg[H];
@@ -176,7 +214,7 @@ __device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         deg[h] = -1;
-        if (u[h] >= 0) deg[h] = (int)(__ldg(P.off + u[h] + 1) - __ldg(P.off + u[h]));
+        if (u[h] >= 0) deg[h] = (int)(__ldg(off + u[h] + 1) - __ldg(off + u[h]));
     }
     if constexpr (kBatch) {
         unsigned long long e = 0;
@@ -190,66 +228,82 @@ __device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>
         for (int h = 0; h < H; ++h) {
             cu[h] = u[h];
             cv[h] = (u[h] >= 0) ? S.v[i0 + h] : 0;
-            if (P.new2old && u[h] >= 0) {
-                cu[h] = __ldg(P.new2old + u[h]);
-                cv[h] = __ldg(P.new2old + cv[h]);
+            if (new2old && u[h] >= 0) {
+                cu[h] = __ldg(new2old + u[h]);
+                cv[h] = __ldg(new2old + cv[h]);
             }
         }
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             if (u[h] < 0) continue;
-            P.dist[cu[h]] = level + 1;
-            if (P.parent) P.parent[cu[h]] = cv[h];
-            if (P.fb[0]) atomicOr(P.fb[(level + 1) % 3] + (u[h] >> 5), 1u << (u[h] & 31));
+            dist[cu[h]] = level + 1;
+            if (parent) parent[cu[h]] = cv[h];
+            if (fbn) atomicOr(fbn + (u[h] >> 5), 1u << (u[h] & 31));
         }
     }
+    // Reserve queue slots and edge ranges for all bins in one round trip:
+    // per bin one warp scan of (entries << 48 | degree sum) -- a lane holds
+    // at most H entries and degrees stay below 2^31, so the sum fits in 48
+    // bits -- then lanes 0..2 issue the bins' atomicAdds together.
+    int bh[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+        bh[h] = deg[h] <= 0 ? -1 : (deg[h] < t_small ? 0 : (deg[h] < t_large ? 1 : 2));
+    unsigned long long incl[kBins], mine[kBins];
+    unsigned long long add = 0ull;
 #pragma unroll
     for (int b = 0; b < kBins; ++b) {
-        int cnt = 0;
-        long long dsum = 0;
+        unsigned long long x = 0ull;
 #pragma unroll
-        for (int h = 0; h < H; ++h) {
-            const int bh = deg[h] <= 0 ? -1 : (deg[h] < P.t_small ? 0 : (deg[h] < P.t_large ? 1 : 2));
-            if (bh == b) {
-                ++cnt;
-                dsum += deg[h];
-            }
-        }
-        if (__ballot_sync(FULL_MASK, cnt > 0) == 0u) continue;
-        const int cincl = warp_incl_scan(cnt);
-        const long long dincl = warp_incl_scan(dsum);
-        const int ctot = __shfl_sync(FULL_MASK, cincl, 31);
-        const long long dtot = __shfl_sync(FULL_MASK, dincl, 31);
-        unsigned long long basep = 0ull;
-        if (lane == 0)
-            basep = atomicAdd(&P.ctl[nslot].packed[b],
-                              ((unsigned long long)ctot << kCountShift) + (unsigned long long)dtot);
-        basep = __shfl_sync(FULL_MASK, basep, 0);
-        long long pos = (long long)(basep >> kCountShift) + (cincl - cnt);
-        long long eo = (long long)(basep & kEdgeMask) + (dincl - dsum);
+        for (int h = 0; h < H; ++h)
+            if (bh[h] == b) x += (1ull << 48) + (unsigned long long)deg[h];
+        mine[b] = x;
+        incl[b] = 0ull;
+        if (__ballot_sync(FULL_MASK, x != 0ull) == 0u) continue;
+        incl[b] = warp_incl_scan(x);
+        const unsigned long long tot = __shfl_sync(FULL_MASK, incl[b], 31);
+        if (lane == (unsigned)b)
+            add = ((tot >> 48) << kCountShift) + (tot & ((1ull << 48) - 1ull));
+    }
+    unsigned long long basep = 0ull;
+    if (add != 0ull) basep = atomicAdd(packed + lane, add);
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        const unsigned long long base = __shfl_sync(FULL_MASK, basep, b);
+        if (mine[b] == 0ull) continue;
+        const unsigned long long excl = incl[b] - mine[b];
+        long long pos = (long long)(base >> kCountShift) + (long long)(excl >> 48);
+        long long eo = (long long)(base & kEdgeMask) + (long long)(excl & ((1ull << 48) - 1ull));
+        // chunk sizes are powers of two: chunk c starts at edge c << cshift
+        const int cshift = b == 1 ? sh_warp : sh_cta;
         const BinQueue& Q = P.q[nxt][b];
-        const long long C = (b == 1) ? P.chunk_warp : P.chunk_cta;
+        int32_t* const qv = Q.v;
+        int64_t* const qe = Q.eoff;
+        int32_t* const qc = Q.chunk;
+        uint64_t* const qm = kBatch ? Q.mask : nullptr;
+        const long long qcap = Q.cap, qccap = Q.chunk_cap;
 #pragma unroll
         for (int h = 0; h < H; ++h) {
-            const int bh = deg[h] <= 0 ? -1 : (deg[h] < P.t_small ? 0 : (deg[h] < P.t_large ? 1 : 2));
-            if (bh != b) continue;
-            if (pos < Q.cap) {
-                Q.v[pos] = u[h];
-                if (kBatch) Q.mask[pos] = S.mask[kBatch ? i0 + h : 0];
+            if (bh[h] != b) continue;
+            if (pos < qcap) {
+                qv[pos] = u[h];
+                if (kBatch) qm[pos] = S.mask[kBatch ? i0 + h : 0];
                 if (b > 0) {
-                    Q.eoff[pos] = eo;
-                    for (long long c = (eo + C - 1) / C; c * C < eo + deg[h]; ++c) {
-                        if (c < Q.chunk_cap) Q.chunk[c] = (int32_t)pos;
-                        else raise_status(P, kDevOverflow);
-                    }
+                    qe[pos] = eo;
+                    // chunks whose first edge lies in [eo, eo + deg) start here
+                    const long long c_end = (eo + deg[h] - 1) >> cshift;
+                    const long long c0 = (eo + (1ll << cshift) - 1) >> cshift;
+                    if (c_end >= qccap) overflow = true;
+                    for (long long c = c0; c <= c_end && c < qccap; ++c) qc[c] = (int32_t)pos;
                 }
             } else {
-                raise_status(P, kDevOverflow);
+                overflow = true;
             }
             ++pos;
             eo += deg[h];
         }
     }
+    if (overflow) raise_status(P, kDevOverflow);
     __syncwarp();
     if (lane == 0) S.cnt = 0;
     __syncwarp();
@@ -418,6 +472,9 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
         return;
     }
     for (int rw = (int)wbase; rw < hi; rw += (int)wstride) {
+        if (P.l2_prefetch && lane == 0 && rw + kPrefetchAhead < hi)
+            prefetch_cols_l2(P.col, a4 + rw + kPrefetchAhead,
+                             a4 + min((long long)hi, rw + kPrefetchAhead + 256));
         const int r0 = rw + 4 * (int)lane;
         const int r1 = r0 + 128;
         int4 x0 = make_int4(0, 0, 0, 0), x1 = make_int4(0, 0, 0, 0);
@@ -515,6 +572,7 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
             a = base + (lo - eo);
             b = base + (hi - eo);
             if (kBatch) mask = __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij);
+            if (P.l2_prefetch) prefetch_cols_l2(P.col, a, min(b, a + kPrefetchAhead));
         }
         const unsigned okb = __ballot_sync(FULL_MASK, ok);
         const long long a4 = a & ~3ll;
@@ -590,8 +648,14 @@ __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int
             const int32_t v = __ldcg(Q.v + ij);
             s_v[threadIdx.x] = v;
             s_eo[threadIdx.x] = eo;
-            s_base[threadIdx.x] = __ldg(P.off + v);
-            s_end[threadIdx.x] = __ldg(P.off + v + 1);
+            const long long base = __ldg(P.off + v), end = __ldg(P.off + v + 1);
+            s_base[threadIdx.x] = base;
+            s_end[threadIdx.x] = end;
+            if (P.l2_prefetch) {
+                const long long a = base + (max(eo, cs) - eo);
+                const long long b = base + (min(eo + (end - base), ce) - eo);
+                prefetch_cols_l2(P.col, a, min(b, a + kPrefetchAhead));
+            }
             if (kBatch)
                 s_mask[kBatch ? threadIdx.x : 0] =
                     __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij);
@@ -639,10 +703,11 @@ __device__ __forceinline__ LevelShape read_level(const TraversalParams& P, int l
     // base chunks (the granularity of the chunk tables), then work items of k
     // base chunks: small levels keep k = 1 so that every CTA / warp gets work,
     // large levels aim at ~4 items per CTA (or warp) to bound per-item costs
+    const int sh_cta = __ffs(P.chunk_cta) - 1, sh_warp = __ffs(P.chunk_warp) - 1;
     const long long base_cta =
-        min((s.edges[2] + P.chunk_cta - 1) / P.chunk_cta, (long long)P.q[cur][2].chunk_cap);
+        min((s.edges[2] + P.chunk_cta - 1) >> sh_cta, (long long)P.q[cur][2].chunk_cap);
     const long long base_warp =
-        min((s.edges[1] + P.chunk_warp - 1) / P.chunk_warp, (long long)P.q[cur][1].chunk_cap);
+        min((s.edges[1] + P.chunk_warp - 1) >> sh_warp, (long long)P.q[cur][1].chunk_cap);
     s.k_cta = pow2_floor_clamped(base_cta / (4ll * gridDim.x), 32);
     s.k_warp = pow2_floor_clamped(base_warp / (4ll * gridDim.x * kWarps), 16);
     s.n_cta = (base_cta + s.k_cta - 1) / s.k_cta;
@@ -979,10 +1044,13 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
     stage_init(S);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    stamp(P, 0);
     init_plain(P, tid, nthreads);
     if (grid_barrier(P)) {
+        stamp(P, 1);
         seed_plain(P, S);
         if (grid_barrier(P)) {
+            stamp(P, 2);
             long long seen_edges = 0;  // edges of all frontiers so far (same in every CTA)
             bool prev_bu = false;
             for (int level = 0;; ++level) {
@@ -1000,6 +1068,7 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
                 expand_level<false>(P, S, L, level, s_hot, dir);
                 prev_bu = dir == 2;
                 if (!grid_barrier(P)) break;
+                stamp(P, 3 + level);
             }
         }
     }

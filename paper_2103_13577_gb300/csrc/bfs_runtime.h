@@ -90,6 +90,9 @@ struct bfs_graph {
     int32_t dir_mode = 0;             // 0 top-down, 1 direction-optimizing, 2 bottom-up always
     int32_t do_alpha = 15, do_beta = 18;
     int32_t bitmap_div = 0;           // bitmap top-down when frontier > n / bitmap_div
+    int32_t l2_prefetch = 0;          // bulk L2 prefetch of bin 1 / bin 2 column segments
+    uint64_t* timeline = nullptr;     // diagnostics: device array of level timestamps
+    int32_t timeline_cap = 0;
     int64_t n_nonzero = 0;            // vertices with out-degree > 0
     bool symmetric = false;           // every edge stored in both directions
     std::mutex mu;

@@ -2,9 +2,12 @@
 16) and runs two single-source traversals with BFS_HOST_LOOP, so that each
 BFS level is its own kernel launch (one ncu result per level).
 
-  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent|do]
+  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent|do|timeline]
 
 do: host-loop launches with the direction-optimizing mode.
+timeline: persistent launches with the level timeline attached; prints the
+median time of init, seed and every level over 8 roots, for the L2 column
+prefetch off and on, top-down and direction-optimizing.
 """
 from __future__ import annotations
 
@@ -29,6 +32,11 @@ def main():
     n = len(off) - 1
     dist = torch.empty(n, dtype=torch.int32, device="cuda")
     par = torch.empty(n, dtype=torch.int32, device="cuda")
+    if mode == "timeline":
+        timeline(bfs, g, graphgen.pick_roots(off, 8, seed=3), dist, par)
+        g.close()
+        ctx.close()
+        return
     flags = bfs.BFS_HOST_LOOP if mode in ("hostloop", "do") else 0
     if mode == "do":
         g.set_option(bfs.BFS_OPT_DIRECTION, 1)
@@ -37,6 +45,38 @@ def main():
         print(g.sync(), flush=True)
     g.close()
     ctx.close()
+
+
+def timeline(bfs, g, roots, dist, par):
+    import numpy as np
+    import torch
+
+    stamps = torch.zeros(64, dtype=torch.int64, device="cuda")
+    bfs.bfs_debug_set_timeline(g.handle, stamps)
+    for direction in (0, 1):
+        g.set_option(bfs.BFS_OPT_DIRECTION, direction)
+        for pf in (0, 1):
+            g.set_option(bfs.BFS_OPT_L2_PREFETCH, pf)
+            rows = []
+            for rep in range(2):
+                for r in roots:
+                    stamps.zero_()
+                    g.run(int(r), dist, par)
+                    st = g.sync()
+                    t = stamps.cpu().numpy()
+                    k = 3 + st["levels"]
+                    if rep == 1:
+                        rows.append(np.diff(t[:k]) / 1e3)
+            width = max(len(x) for x in rows)
+            a = np.full((len(rows), width), np.nan)
+            for i, x in enumerate(rows):
+                a[i, :len(x)] = x
+            med = np.nanmedian(a, axis=0)
+            tot = np.median([x.sum() for x in rows])
+            names = ["init", "seed"] + [f"L{i}" for i in range(width - 2)]
+            print(f"direction {direction} prefetch {pf} total_us {tot:.1f} " +
+                  " ".join(f"{nm}={v:.1f}" for nm, v in zip(names, med)), flush=True)
+    bfs.bfs_debug_set_timeline(g.handle, None)
 
 
 if __name__ == "__main__":

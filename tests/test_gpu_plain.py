@@ -343,3 +343,13 @@ def test_stream_ordering_on_torch_stream(ctx, kron16):
         d_ref, _, _ = oracle.bfs(off, col, int(r))
         assert np.array_equal(d.cpu().numpy(), d_ref)
     g.close()
+
+
+def test_chunk_sizes_must_be_powers_of_two(ctx, kron16):
+    off, col, _ = kron16
+    g = bfs.Graph(ctx, off, col)
+    for bins in ((32, 4096, 384, 2048), (32, 4096, 512, 3072), (32, 4096, 64, 2048)):
+        with pytest.raises(bfs.BfsError):
+            g.set_bins(*bins)
+    g.set_bins(32, 4096, 256, 1024)
+    g.close()
