@@ -165,6 +165,15 @@ __device__ void kernel_exit(const TraversalParams& P) {
 #define BFS_STAGE_CAP 64
 #endif
 constexpr int kStageCap = BFS_STAGE_CAP;
+// A probe round whose warp holds at least this many candidates claims them
+// at once (one atomic round trip shared by all of them); rounds with fewer
+// leave the claim to the stage flush.
+#ifndef BFS_CLAIM_NOW
+#define BFS_CLAIM_NOW 16
+#endif
+constexpr int kClaimNow = BFS_CLAIM_NOW;
+// Parent field flag of a staged entry that is already claimed.
+constexpr uint32_t kClaimed = 0x80000000u;
 
 template <bool kBatch>
 struct Stage {
@@ -175,6 +184,7 @@ struct Stage {
     unsigned long long edges;                          // batched: sum deg * lanes
     const uint32_t* hot;                               // plain: shared copy of visited[0, hot_bits)
     int hot_bits;                                      // 0 when the copy is off for this level
+    int disc;                                          // plain: vertices this warp claimed
 };
 
 // Warp-collective flush of the staged entries into the next frontier.
@@ -211,6 +221,45 @@ __device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>
     int deg[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) u[h] = (i0 + h < n) ? S.u[i0 + h] : -1;
+    // Plain entries are candidates (their target looked unvisited when it
+    // was probed): the claim -- an atomicOr on the visited bitmap whose old
+    // value says who set the bit first -- happens here, for all of a flush's
+    // entries at once, instead of one round trip per probe round.
+    uint32_t old[H];
+    uint32_t pv[H];  // plain: staged parent with the claimed flag
+    if constexpr (!kBatch) {
+        uint32_t* const visited = P.visited;
+#pragma unroll
+        for (int h = 0; h < H; ++h) pv[h] = u[h] >= 0 ? (uint32_t)S.v[i0 + h] : 0u;
+        if (P.use_match_any) {
+            // lanes claiming bits of the same word merge them: one atomicOr
+            // per word, the first lane holding a vertex wins it
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                old[h] = (u[h] >= 0 && (pv[h] & kClaimed)) ? 0u : 0xffffffffu;
+                const bool need = u[h] >= 0 && !(pv[h] & kClaimed);
+                const unsigned needm = __ballot_sync(FULL_MASK, need);
+                if (need) {
+                    const uint32_t bit = 1u << (u[h] & 31);
+                    const unsigned peers = __match_any_sync(needm, u[h] >> 5);
+                    const uint32_t bits = __reduce_or_sync(peers, bit);
+                    const int leader = __ffs(peers) - 1;
+                    uint32_t o = 0u;
+                    if ((int)lane == leader) o = atomicOr(visited + (u[h] >> 5), bits);
+                    o = __shfl_sync(peers, o, leader);
+                    const unsigned same = __match_any_sync(peers, u[h]);
+                    if ((o & bit) == 0u && (int)lane == __ffs(same) - 1) old[h] = 0u;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < H; ++h) {
+                old[h] = 0xffffffffu;
+                if (u[h] >= 0)
+                    old[h] = (pv[h] & kClaimed) ? 0u : atomicOr(visited + (u[h] >> 5), 1u << (u[h] & 31));
+            }
+        }
+    }
 #pragma unroll
     for (int h = 0; h < H; ++h) {
         deg[h] = -1;
@@ -227,12 +276,23 @@ __device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             cu[h] = u[h];
-            cv[h] = (u[h] >= 0) ? S.v[i0 + h] : 0;
+            cv[h] = (u[h] >= 0) ? (int32_t)(pv[h] & ~kClaimed) : 0;
             if (new2old && u[h] >= 0) {
                 cu[h] = __ldg(new2old + u[h]);
                 cv[h] = __ldg(new2old + cv[h]);
             }
         }
+        // entries whose claim lost are dropped
+        int won = 0;
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            if (u[h] >= 0 && ((old[h] >> (u[h] & 31)) & 1u)) {
+                u[h] = -1;
+                deg[h] = -1;
+            }
+            won += __popc(__ballot_sync(FULL_MASK, u[h] >= 0));
+        }
+        if (lane == 0) S.disc += won;
 #pragma unroll
         for (int h = 0; h < H; ++h) {
             if (u[h] < 0) continue;
@@ -341,19 +401,66 @@ __device__ __forceinline__ void stage_init(Stage<kBatch>& S) {
         S.edges = 0ull;
         S.hot = nullptr;
         S.hot_bits = 0;
+        S.disc = 0;
     }
     __syncwarp();
 }
 
 // ----------------------------------------------------------------- visits
+// Stages each lane's candidates (bit j of candm: u[j] with parent v[j],
+// flag kClaimed when already claimed) in one pass: a warp scan of the
+// per-lane counts places them; a full stage is flushed and the rest placed
+// after it.
+template <int K>
+__device__ __forceinline__ void stage_push_multi(const TraversalParams& P, Stage<false>& S,
+                                                 unsigned candm, const int32_t (&u)[K],
+                                                 const int32_t (&v)[K], uint32_t flag, int level,
+                                                 int nxt, int nslot) {
+    const int c = __popc(candm);
+    if (__ballot_sync(FULL_MASK, c != 0) == 0u) return;
+    const int incl = warp_incl_scan(c);
+    const int total = __shfl_sync(FULL_MASK, incl, 31);
+    const int excl = incl - c;
+    for (int done = 0; done < total;) {
+        int n0 = S.cnt;
+        if (n0 == kStageCap) {
+            stage_flush<false>(P, S, level, nxt, nslot);
+            n0 = 0;
+        }
+        const int take = min(kStageCap - n0, total - done);
+        int k = excl - done;  // stage offset of this lane's next candidate
+#pragma unroll
+        for (int j = 0; j < K; ++j) {
+            if ((candm >> j) & 1u) {
+                if (k >= 0 && k < take) {
+                    S.u[n0 + k] = u[j];
+                    S.v[n0 + k] = (int32_t)((uint32_t)v[j] | flag);
+                }
+                ++k;
+            }
+        }
+        __syncwarp();
+        if (lane_id() == 0) S.cnt = n0 + take;
+        __syncwarp();
+        done += take;
+    }
+}
+
 // K edges per lane at once: all K visited-bitmap probes are issued before
-// any result is used, then the atomics, so a warp keeps K random accesses
-// in flight instead of one.  Winners only go to the warp's stage.
+// any result is used, so a warp keeps K random reads in flight instead of
+// one.  A probe that finds the bit clear makes the edge a candidate.  The
+// claim (the atomicOr whose old value decides which edge discovers the
+// vertex) is made here when the round has many candidates -- discovery-
+// heavy levels, where claiming early also keeps other warps from staging
+// the same vertex -- and otherwise left to the stage flush, which claims a
+// whole stage in one round trip instead of one per probe round.  A stale
+// cached word can only show clear a bit that is already set (bits are never
+// cleared during a traversal), and the claim then rejects the candidate.
 template <int K>
 __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<false>& S,
                                               unsigned okm, const int32_t (&u)[K],
                                               const int32_t (&v)[K], int level, int nxt,
-                                              int nslot, int& my_disc) {
+                                              int nslot) {
     // pass 1 (shared memory only): drop edges whose target was visited before
     // the level and lies in the hot prefix copied at level start
     const int hot_bits = S.hot_bits;
@@ -368,40 +475,23 @@ __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<fa
     uint32_t w[K];
 #pragma unroll
     for (int j = 0; j < K; ++j) w[j] = ((okm >> j) & 1u) ? P.visited[u[j] >> 5] : 0xffffffffu;
-    unsigned winm = 0u;
-    if (P.use_match_any) {
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const uint32_t bit = 1u << (u[j] & 31);
-            const bool need = (w[j] & bit) == 0u;
-            const unsigned needm = __ballot_sync(FULL_MASK, need);
-            if (need) {
-                const unsigned peers = __match_any_sync(needm, u[j] >> 5);
-                const uint32_t bits = __reduce_or_sync(peers, bit);
-                const int leader = __ffs(peers) - 1;
-                uint32_t old = 0u;
-                if ((int)lane_id() == leader) old = atomicOr(P.visited + (u[j] >> 5), bits);
-                old = __shfl_sync(peers, old, leader);
-                const unsigned same = __match_any_sync(peers, u[j]);
-                if (((old & bit) == 0u) && ((int)lane_id() == __ffs(same) - 1)) winm |= 1u << j;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < K; ++j) {
-            const uint32_t bit = 1u << (u[j] & 31);
-            if ((w[j] & bit) == 0u) w[j] = atomicOr(P.visited + (u[j] >> 5), bit);
-            else w[j] = bit;
-        }
-#pragma unroll
-        for (int j = 0; j < K; ++j)
-            if ((w[j] & (1u << (u[j] & 31))) == 0u) winm |= 1u << j;
-    }
-    if (__ballot_sync(FULL_MASK, winm != 0u) == 0u) return;
-    my_disc += __popc(winm);
+    unsigned candm = 0u;
 #pragma unroll
     for (int j = 0; j < K; ++j)
-        stage_push<false>(P, S, (winm >> j) & 1u, u[j], v[j], 0ull, level, nxt, nslot);
+        if (((w[j] >> (u[j] & 31)) & 1u) == 0u) candm |= 1u << j;
+    const int total = __reduce_add_sync(FULL_MASK, (unsigned)__popc(candm));
+    if (total == 0) return;
+    uint32_t flag = 0u;
+    if (total >= kClaimNow) {
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if ((candm >> j) & 1u) w[j] = atomicOr(P.visited + (u[j] >> 5), 1u << (u[j] & 31));
+#pragma unroll
+        for (int j = 0; j < K; ++j)
+            if (((w[j] >> (u[j] & 31)) & 1u) != 0u) candm &= ~(1u << j);
+        flag = kClaimed;
+    }
+    stage_push_multi<K>(P, S, candm, u, v, flag, level, nxt, nslot);
 }
 
 // Batched traversal, phase A: OR the lanes of the frontier entry that u has
@@ -428,10 +518,9 @@ __device__ __forceinline__ void visit_batch_k(const TraversalParams& P, unsigned
 template <bool kBatch, int K>
 __device__ __forceinline__ void visit_k(const TraversalParams& P, Stage<kBatch>& S, unsigned okm,
                                         const int32_t (&u)[K], const int32_t (&v)[K],
-                                        const uint64_t (&mask)[K], int level, int nxt, int nslot,
-                                        int& my_disc) {
+                                        const uint64_t (&mask)[K], int level, int nxt, int nslot) {
     if constexpr (kBatch) visit_batch_k<K>(P, okm, u, mask);
-    else visit_plain_k<K>(P, S, okm, u, v, level, nxt, nslot, my_disc);
+    else visit_plain_k<K>(P, S, okm, u, v, level, nxt, nslot);
 }
 
 // ------------------------------------------------------------ expansion
@@ -444,7 +533,7 @@ template <bool kBatch>
 __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<kBatch>& S,
                                                long long a, long long b, int32_t v, uint64_t mask,
                                                int level, int nxt, int nslot, long long wbase,
-                                               long long wstride, int& my_disc) {
+                                               long long wstride) {
     const unsigned lane = lane_id();
     const long long a4 = a & ~3ll;
     const int lo = (int)(a - a4);                 // valid entries: [lo, hi) relative to a4
@@ -468,7 +557,7 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
         const int32_t u[4] = {x0.x, x0.y, x0.z, x0.w};
         const int32_t v4[4] = {v, v, v, v};
         const uint64_t m4[4] = {mask, mask, mask, mask};
-        visit_k<kBatch, 4>(P, S, okm, u, v4, m4, level, nxt, nslot, my_disc);
+        visit_k<kBatch, 4>(P, S, okm, u, v4, m4, level, nxt, nslot);
         return;
     }
     for (int rw = (int)wbase; rw < hi; rw += (int)wstride) {
@@ -487,7 +576,7 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
             if (r1 + j >= lo && r1 + j < hi) okm |= 1u << (4 + j);
         }
         const int32_t u[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
+        visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot);
     }
 }
 
@@ -497,8 +586,7 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
 // shuffle binary search over the scan.
 template <bool kBatch>
 __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, int cur,
-                                   long long grp, long long cnt, int level, int nxt, int nslot,
-                                   int& my_disc) {
+                                   long long grp, long long cnt, int level, int nxt, int nslot) {
     const BinQueue& Q = P.q[cur][0];
     const unsigned lane = lane_id();
     const long long i = grp * 32 + lane;
@@ -538,7 +626,7 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
                 u[j] = __ldcs(P.col + bo + (e - xo));
             }
         }
-        visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
+        visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot);
     }
 }
 
@@ -551,7 +639,7 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
 template <bool kBatch>
 __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
                                   long long item, int k, long long cnt, long long E, int level,
-                                  int nxt, int nslot, int& my_disc) {
+                                  int nxt, int nslot) {
     const BinQueue& Q = P.q[cur][1];
     const unsigned lane = lane_id();
     const long long cs = item * k * (long long)P.chunk_warp;
@@ -618,7 +706,7 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
                     mm[4 * h + c] = mo;
                 }
             }
-            visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
+            visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot);
         }
         if (__popc(okb) < 32) break;
         i += 32;
@@ -630,7 +718,7 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
 template <bool kBatch>
 __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
                                  long long item, int k, long long cnt, long long E, int level,
-                                 int nxt, int nslot, int& my_disc) {
+                                 int nxt, int nslot) {
     __shared__ long long s_eo[kBlock], s_base[kBlock], s_end[kBlock];
     __shared__ int32_t s_v[kBlock];
     __shared__ unsigned long long s_mask[kBatch ? kBlock : 1];
@@ -666,7 +754,7 @@ __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int
             const long long lo = max(eok, cs), hi = min(eok + (s_end[k] - bk), ce);
             expand_segment<kBatch>(P, S, bk + (lo - eok), bk + (hi - eok), s_v[k],
                                    kBatch ? s_mask[kBatch ? k : 0] : 0ull, level, nxt, nslot,
-                                   (long long)warp * 256, 256ll * kWarps, my_disc);
+                                   (long long)warp * 256, 256ll * kWarps);
         }
         __syncthreads();
         if (nent < kBlock) break;
@@ -729,7 +817,7 @@ __device__ __forceinline__ LevelShape read_level(const TraversalParams& P, int l
 // atomics.  Found vertices go through the same stage as top-down winners
 // (distance level + 1, parent = the frontier neighbour, next frontier).
 __device__ void bottom_up_level(const TraversalParams& P, Stage<false>& S, int level, int nxt,
-                                int nslot, int& my_disc) {
+                                int nslot) {
     const uint32_t* F = P.fb[level % 3];
     const unsigned lane = lane_id();
     const long long words = (P.bu_limit + 31) / 32;
@@ -758,10 +846,8 @@ __device__ void bottom_up_level(const TraversalParams& P, Stage<false>& S, int l
                 if ((F[u0 >> 5] >> (u0 & 31)) & 1u) { found = true; par = u0; }
             }
         }
-        const unsigned fm = __ballot_sync(FULL_MASK, found);
-        if (fm == 0u) continue;
-        if (lane == 0) P.visited[w] = vis | fm;
-        my_disc += found ? 1 : 0;
+        // the warp is the only one looking at word w, so the flush's claim of
+        // a found vertex always wins
         stage_push<false>(P, S, found, (int32_t)v, par, 0ull, level, nxt, nslot);
     }
 }
@@ -785,7 +871,7 @@ __device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
 // one id range with adjacent rows, so a tile's column reads are close to
 // one stream.  The heavier bins keep their (balanced) queues.
 __device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, long long tile,
-                                   int level, int nxt, int nslot, int& my_disc) {
+                                   int level, int nxt, int nslot) {
     const uint32_t* F = P.fb[level % 3];
     const unsigned lane = lane_id();
     const long long words = (P.n + 31) / 32;
@@ -858,7 +944,7 @@ __device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, lo
                     mm[4 * h + c] = 0ull;
                 }
             }
-            visit_k<false, 8>(P, S, okm, u, vv, mm, level, nxt, nslot, my_disc);
+            visit_k<false, 8>(P, S, okm, u, vv, mm, level, nxt, nslot);
         }
     }
 }
@@ -868,7 +954,7 @@ __device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, lo
 // (bin 1 chunks, bin 0 groups) dealt round robin over all warps of the grid.
 template <bool kBatch>
 __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
-                                int level, int& my_disc, bool bitmap = false) {
+                                int level, bool bitmap = false) {
     __shared__ long long s_item;
     const int slot = level % 3, nslot = (level + 1) % 3;
     const int cur = level & 1, nxt = cur ^ 1;
@@ -881,7 +967,7 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
             __syncthreads();
             if (item >= L.n_cta) break;
             expand_cta_chunk<kBatch>(P, S, cur, item, L.k_cta, L.cnt[2], L.edges[2], level, nxt,
-                                     nslot, my_disc);
+                                     nslot);
         }
     }
     const long long nwarps = (long long)gridDim.x * kWarps;
@@ -898,16 +984,15 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
     for (long long it = gw; it < witems; it += nwarps) {
         if (it < L.chunks_warp) {
             expand_warp_chunk<kBatch>(P, S, cur, it, L.k_warp, L.cnt[1], L.edges[1], level, nxt,
-                                      nslot, my_disc);
+                                      nslot);
         } else if constexpr (!kBatch) {
             if (bitmap)
-                expand_bitmap_tile(P, S, tile0 + (it - L.chunks_warp), level, nxt, nslot, my_disc);
+                expand_bitmap_tile(P, S, tile0 + (it - L.chunks_warp), level, nxt, nslot);
             else
                 expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt,
-                                           nslot, my_disc);
+                                           nslot);
         } else {
-            expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt, nslot,
-                                       my_disc);
+            expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt, nslot);
         }
     }
 }
@@ -918,8 +1003,8 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
     __shared__ int s_disc;
     const int nslot = (level + 1) % 3;
     const int nxt = (level & 1) ^ 1;
-    int my_disc = 0;
     if (threadIdx.x == 0) s_disc = 0;
+    if (lane_id() == 0) S.disc = 0;
     if (!kBatch) {
         // large levels: copy the hot prefix of the visited bitmap (after the
         // degree-ordered renumbering, the highest-degree vertices) into
@@ -943,15 +1028,14 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
     bool bottom_up = false;
     if constexpr (!kBatch) {
         if (dir == 2) {
-            bottom_up_level(P, S, level, nxt, nslot, my_disc);
+            bottom_up_level(P, S, level, nxt, nslot);
             bottom_up = true;
         }
     }
-    if (!bottom_up) expand_top_down<kBatch>(P, S, L, level, my_disc, dir == 1);
+    if (!bottom_up) expand_top_down<kBatch>(P, S, L, level, dir == 1);
     stage_flush<kBatch>(P, S, level, nxt, nslot);
     if (!kBatch) {
-        const int wd = warp_incl_scan(my_disc);
-        if (lane_id() == 31 && wd > 0) atomicAdd(&s_disc, wd);
+        if (lane_id() == 0 && S.disc > 0) atomicAdd(&s_disc, S.disc);
         __syncthreads();
         if (threadIdx.x == 0 && s_disc > 0) atomicAdd(&P.ctl[nslot].discovered, (unsigned)s_disc);
     }
@@ -1000,10 +1084,7 @@ __device__ void seed_plain(const TraversalParams& P, Stage<false>& S) {
     if (blockIdx.x != 0 || threadIdx.x >= 32) return;
     const bool l0 = threadIdx.x == 0;
     const int32_t root = P.old2new ? __ldg(P.old2new + P.root_caller) : P.root_caller;
-    if (l0) {
-        P.visited[root >> 5] |= 1u << (root & 31);
-        P.ctl[0].discovered = 1u;
-    }
+    if (l0) P.ctl[0].discovered = 1u;
     // staged with level -1 and itself as parent: the flush writes dist 0 and
     // parent = root, and queues the root in the bin of its degree
     stage_push<false>(P, S, l0, root, root, 0ull, -1, 0, 0);
