@@ -112,7 +112,7 @@ bfs_status bfs_graph_get_info(const bfs_graph* g, bfs_graph_info* out);
 /* Degree-bin thresholds and base chunk sizes (the autotuner's knobs).
  * t_small >= 1, t_large > t_small, chunk_warp a power of two in
  * [128, 2^24], chunk_cta a power of two in [1024, 2^24] (chunk starts are
- * found with shifts).  Defaults 32, 4096, 512, 2048.  Reallocates the per-traversal buffers;
+ * found with shifts).  Defaults 16, 4096, 128, 1024.  Reallocates the per-traversal buffers;
  * must not be called while a traversal on g is in flight. */
 bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
                               int32_t chunk_warp, int32_t chunk_cta);
@@ -126,7 +126,7 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *                            with BFS_ERR_TIMEOUT.
  *   BFS_OPT_CTAS_PER_SM      2, 3 or 4: resident CTAs per SM of the traversal
  *                            kernels (register cap 128, 80 or 64; batched
- *                            kernels use 3 when 4 is asked; default 3).
+ *                            kernels use 3 when 4 is asked; default 4).
  *   BFS_OPT_HOT_WORDS        visited-bitmap words (multiple of 4, <= 40960)
  *                            each CTA copies to shared memory at the start of
  *                            a large level; probes of vertices below 32x that

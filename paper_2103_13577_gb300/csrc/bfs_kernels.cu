@@ -193,14 +193,15 @@ struct Stage {
 // issued by lanes 0..2 at once, places the lane's entries at consecutive
 // queue slots.
 //
-// The function is out of line (it is called from many places), so P
-// arrives as a generic pointer into the launch parameters.  Fields are read
-// into registers before the stores that follow them: a read after a store
-// through a generic pointer cannot be moved above it (the compiler cannot
-// rule out that the store changed the parameter), and re-reads inside the
-// store loops would put a round trip on every iteration.
+// The flush is inlined at every call site: as an out-of-line call it made
+// the callers save their live registers around it (spills on the probe
+// loops' critical path).  Launch parameters are still read into registers
+// before the stores that follow them: P is a reference, and a parameter read
+// after a global store through a generic pointer cannot be moved above it
+// (the compiler cannot rule out that the store changed the parameter), which
+// would put a round trip on every chunk-table iteration.
 template <bool kBatch>
-__device__ __noinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>& S, int level,
+__device__ __forceinline__ void stage_flush(const TraversalParams& P, Stage<kBatch>& S, int level,
                                          int nxt, int nslot) {
     constexpr int H = kStageCap / 32;
     const unsigned lane = lane_id();

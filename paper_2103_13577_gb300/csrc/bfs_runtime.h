@@ -74,7 +74,7 @@ struct bfs_graph {
     int32_t* d_new2old = nullptr;     // device numbering -> caller numbering
     int32_t* d_old2new = nullptr;     // caller numbering -> device numbering
     bool relabelled = false;
-    int32_t t_small = 32, t_large = 4096, chunk_warp = 512, chunk_cta = 2048;
+    int32_t t_small = 16, t_large = 4096, chunk_warp = 128, chunk_cta = 1024;
     uint64_t bin_count[bfs::kBins] = {0, 0, 0};
     uint64_t bin_edges[bfs::kBins] = {0, 0, 0};
     bfs::Workspace* ws_plain = nullptr;
@@ -84,7 +84,7 @@ struct bfs_graph {
     int32_t debug_stall = 0;
     long long timeout_ns = 2000000000ll;
     int32_t use_match_any = 0;
-    int32_t min_blocks = 3;           // resident CTAs per SM the kernels are built for
+    int32_t min_blocks = 4;           // resident CTAs per SM the kernels are built for
     int32_t hot_words = 0;            // visited words kept in shared memory on large levels
     long long hot_min_edges = 1ll << 20;
     int32_t dir_mode = 0;             // 0 top-down, 1 direction-optimizing, 2 bottom-up always
