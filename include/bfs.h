@@ -369,14 +369,15 @@ int32_t bfs_version(void);
  * restores normal operation (default limit). */
 bfs_status bfs_debug_set_barrier_test(bfs_graph* g, int32_t stall, int64_t timeout_ns);
 
-/* Level timeline of the persistent single-source traversal (bfs_run without
- * BFS_HOST_LOOP).  d_stamps: device array of cap >= 3 uint64 entries, owned
- * by the caller and kept alive while traversals run; nullptr turns the
- * timeline off (default).  Each traversal writes %globaltimer (ns) into
- * d_stamps[0] at kernel start, [1] after the initialisation barrier, [2]
- * after the root is seeded and [3 + L] after level L's barrier, for as many
- * levels as fit; entries past the last level are left unwritten.  The
- * timestamps cost one store per level. */
+/* Level timeline of the persistent traversals (bfs_run and bfs_run_batch
+ * without BFS_HOST_LOOP).  d_stamps: device array of cap >= 3 uint64
+ * entries, owned by the caller and kept alive while traversals run; nullptr
+ * turns the timeline off (default).  Each traversal writes %globaltimer (ns)
+ * into d_stamps[0] at kernel start, [1] after the initialisation barrier,
+ * [2] after the roots are seeded, then single-source: [3 + L] after level
+ * L's barrier; batched: [3 + 2L] after level L's expansion and [4 + 2L]
+ * after its sweep -- for as many entries as fit; later entries are left
+ * unwritten.  The timestamps cost one store per barrier. */
 bfs_status bfs_debug_set_timeline(bfs_graph* g, uint64_t* d_stamps, int32_t cap);
 
 #ifdef __cplusplus

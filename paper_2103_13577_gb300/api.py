@@ -183,8 +183,9 @@ def bfs_butterfly_schedule(nodes: int, fanout: int, round_: int, node: int) -> l
 
 def bfs_debug_set_timeline(g: int, stamps) -> None:
     """Attach a device int64 tensor (>= 3 entries) that every persistent
-    single-source traversal fills with %globaltimer stamps: [0] start, [1]
-    after init, [2] after the seed, [3 + L] after level L.  None detaches."""
+    traversal fills with %globaltimer stamps: [0] start, [1] after init, [2]
+    after the seed; single-source [3 + L] after level L, batched [3 + 2L]
+    after level L's expansion and [4 + 2L] after its sweep.  None detaches."""
     if stamps is None:
         check(_lib.lib().bfs_debug_set_timeline(g, None, 0), "bfs_debug_set_timeline")
         return

@@ -74,8 +74,7 @@ struct TraversalParams {
     GridBarrier* bar;
     DevStats* stats;
     // batched traversal state
-    uint64_t* lane_visited;   // [n]
-    uint64_t* lane_next;      // [n]
+    uint64_t* lane_vn;        // [n][2]: lanes that reached v (visited), lanes reaching v next
     uint8_t* lane_level;      // [n][64]: level of each lane at each vertex
     int32_t nlanes;
     int32_t dist_int8;

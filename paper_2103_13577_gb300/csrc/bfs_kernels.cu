@@ -503,17 +503,19 @@ template <int K>
 __device__ __forceinline__ void visit_batch_k(const TraversalParams& P, unsigned okm,
                                               const int32_t (&u)[K],
                                               const uint64_t (&mask)[K]) {
-    uint64_t m[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) m[j] = ((okm >> j) & 1u) ? (mask[j] & ~P.lane_visited[u[j]]) : 0ull;
-    uint64_t nx[K];
-#pragma unroll
-    for (int j = 0; j < K; ++j) nx[j] = m[j] ? P.lane_next[u[j]] : ~0ull;
+    // visited and next of a vertex are adjacent: one 16-byte load each
+    ulonglong2 vn[K];
 #pragma unroll
     for (int j = 0; j < K; ++j)
-        if ((m[j] & ~nx[j]) != 0ull)
-            atomicOr(reinterpret_cast<unsigned long long*>(P.lane_next + u[j]),
-                     (unsigned long long)m[j]);
+        vn[j] = ((okm >> j) & 1u) ? *reinterpret_cast<const ulonglong2*>(P.lane_vn + 2 * (long long)u[j])
+                                  : make_ulonglong2(~0ull, ~0ull);
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        const uint64_t m = mask[j] & ~vn[j].x;
+        if ((m & ~vn[j].y) != 0ull)
+            atomicOr(reinterpret_cast<unsigned long long*>(P.lane_vn + 2 * (long long)u[j] + 1),
+                     (unsigned long long)m);
+    }
 }
 
 template <bool kBatch, int K>
@@ -1193,8 +1195,7 @@ __device__ void init_batch(const TraversalParams& P, long long tid, long long nt
         P.stats->status = 0;
         P.stats->max_level = 0;
     }
-    fill_u64(P.lane_visited, P.n, tid, nthreads);
-    fill_u64(P.lane_next, P.n, tid, nthreads);
+    fill_u64(P.lane_vn, 2 * P.n, tid, nthreads);
     // distances are not filled here: emit_batch writes every (lane, vertex)
 }
 
@@ -1218,7 +1219,7 @@ __device__ __forceinline__ void record_lane_level(const TraversalParams& P, int 
 __device__ void emit_batch(const TraversalParams& P, long long tid, long long nthreads) {
     for (long long c = tid; c < P.n; c += nthreads) {
         const long long v = P.old2new ? __ldg(P.old2new + c) : c;
-        const uint64_t vis = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_visited) + v);
+        const uint64_t vis = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_vn) + 2 * v);
         const uint4* lv = reinterpret_cast<const uint4*>(P.lane_level + v * 64);
         uint4 q[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0),
                       make_uint4(0, 0, 0, 0)};
@@ -1261,7 +1262,7 @@ __device__ void seed_batch(const TraversalParams& P, Stage<true>& S) {
             }
             r = P.old2new ? __ldg(P.old2new + cr) : cr;
             record_lane_level(P, i, r, cr, 0);
-            if (first) P.lane_visited[r] = mask;
+            if (first) P.lane_vn[2 * (long long)r] = mask;
         }
         stage_push<true>(P, S, first, r, 0, mask, -1, 0, 0);
     }
@@ -1277,6 +1278,17 @@ __device__ void seed_batch(const TraversalParams& P, Stage<true>& S) {
 
 // Phase B of a batched level: lanes that reached v for the first time get
 // distance level + 1 and make v part of the next frontier with those lanes.
+// Byte i of the result is 0xff when bit i of m (8 bits) is set: the bits
+// are spread to one per byte by three shift-or-mask steps, then each 0x01
+// byte is multiplied up to 0xff (no carries between bytes).
+__device__ __forceinline__ unsigned long long byte_mask_of_bits(unsigned m) {
+    unsigned long long x = m & 0xffu;
+    x = (x | (x << 28)) & 0x0000000f0000000full;
+    x = (x | (x << 14)) & 0x0003000300030003ull;
+    x = (x | (x << 7)) & 0x0101010101010101ull;
+    return x * 0xffull;
+}
+
 __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level, long long tid,
                             long long nthreads) {
     const int nslot = (level + 1) % 3, nxt = (level + 1) & 1;
@@ -1285,30 +1297,45 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
     const long long nround = (P.n + 31) / 32 * 32;  // warp-uniform trip count
     for (long long v = tid; v < nround; v += nthreads) {
         uint64_t fresh = 0ull;
+        bool reached_before = false;  // some lane had reached v at an earlier level
         if (v < P.n) {
-            const uint64_t nx = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_next) + v);
-            if (nx != 0ull) {
-                const uint64_t vis =
-                    __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_visited) + v);
-                fresh = nx & ~vis;
-                P.lane_next[v] = 0ull;
-                if (fresh != 0ull) {
-                    P.lane_visited[v] = vis | fresh;
-                    my_pairs += __popcll(fresh);
-                }
+            ulonglong2* const pv = reinterpret_cast<ulonglong2*>(P.lane_vn) + v;
+            const ulonglong2 vn = __ldcg(pv);
+            if (vn.y != 0ull) {
+                fresh = vn.y & ~vn.x;
+                reached_before = vn.x != 0ull;
+                *pv = make_ulonglong2(vn.x | fresh, 0ull);
+                my_pairs += __popcll(fresh);
             }
         }
-        // distances: loop over the union of new lanes in this warp
-        unsigned long long any = fresh;
+        // levels: one read-modify-write of the vertex's 64-byte level row
+        // (16-byte accesses, consecutive vertices' rows adjacent), bytes of
+        // the new lanes set to level + 1; bytes of lanes not reached yet are
+        // never read, so a first visit skips the read
+        if (fresh != 0ull) {
+            uint4* row = reinterpret_cast<uint4*>(P.lane_level + v * 64);
+            uint4 q[4];
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) any |= __shfl_xor_sync(FULL_MASK, any, d);
-        if (any != 0ull) {
-            const int32_t cv =
-                (fresh != 0ull && level + 1 >= 255) ? (P.new2old ? __ldg(P.new2old + v) : (int32_t)v) : 0;
-            while (any != 0ull) {
-                const int li = __ffsll((long long)any) - 1;
-                any &= any - 1ull;
-                if ((fresh >> li) & 1ull) record_lane_level(P, li, v, cv, level + 1);
+            for (int k = 0; k < 4; ++k)
+                q[k] = reached_before ? __ldcg(row + k) : make_uint4(0, 0, 0, 0);
+            const int lvl = level + 1 < 255 ? level + 1 : 255;
+            const unsigned long long lvl8 = (unsigned long long)lvl * 0x0101010101010101ull;
+            unsigned long long* w = reinterpret_cast<unsigned long long*>(q);
+#pragma unroll
+            for (int g = 0; g < 8; ++g) {
+                const unsigned long long bm = byte_mask_of_bits((unsigned)(fresh >> (8 * g)) & 0xffu);
+                w[g] = (w[g] & ~bm) | (lvl8 & bm);
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) row[k] = q[k];
+            if (level + 1 >= 255) {
+                // deep levels: the distance goes straight to the output
+                const int32_t cv = P.new2old ? __ldg(P.new2old + v) : (int32_t)v;
+                for (unsigned long long f = fresh; f != 0ull; f &= f - 1ull) {
+                    const long long idx = (long long)(__ffsll((long long)f) - 1) * P.n + cv;
+                    if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)(level + 1);
+                    else P.dist[idx] = level + 1;
+                }
             }
         }
         stage_push<true>(P, S, fresh != 0ull, (int32_t)(v < P.n ? v : 0), 0, fresh, level, nxt,
@@ -1343,10 +1370,13 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
     stage_init(S);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    stamp(P, 0);
     init_batch(P, tid, nthreads);
     if (grid_barrier(P)) {
+        stamp(P, 1);
         seed_batch(P, S);
         if (grid_barrier(P)) {
+            stamp(P, 2);
             for (int level = 0;; ++level) {
                 const LevelShape L = read_level(P, level);
                 if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) break;
@@ -1357,8 +1387,10 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
                 book_batch_level(P, level);
                 expand_level<true>(P, S, L, level, nullptr);
                 if (!grid_barrier(P)) break;
+                stamp(P, 3 + 2 * level);
                 sweep_batch(P, S, level, tid, nthreads);
                 if (!grid_barrier(P)) break;
+                stamp(P, 4 + 2 * level);
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
                     if (__ldcg(reinterpret_cast<const unsigned long long*>(
                             &P.ctl[(level + 1) % 3].new_lanes)) > 0ull)

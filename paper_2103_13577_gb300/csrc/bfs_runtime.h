@@ -47,8 +47,7 @@ struct Workspace {
     GridBarrier* bar = nullptr;
     DevStats* stats = nullptr;
     uint32_t* fb[3] = {nullptr, nullptr, nullptr};  // plain: frontier bitmaps
-    uint64_t* lane_visited = nullptr;
-    uint64_t* lane_next = nullptr;
+    uint64_t* lane_vn = nullptr;       // batched: [n][2] visited / next lane sets
     uint8_t* lane_level = nullptr;     // batched: [n][64] level bytes
     int32_t* roots = nullptr;          // [64]
     int32_t* dist_scratch = nullptr;   // host-output staging (plain: n; batched: none)
