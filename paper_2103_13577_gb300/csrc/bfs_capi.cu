@@ -253,7 +253,10 @@ static void fill_params(bfs_graph* g, Workspace* ws, TraversalParams& P) {
     P.use_match_any = g->use_match_any;
     P.hot_words = g->hot_words;
     P.hot_min_edges = g->hot_min_edges;
-    for (int f = 0; f < 3; ++f) P.fb[f] = ws->fb[f];
+    // the frontier bitmaps serve bottom-up and bitmap-order levels only; a
+    // traversal that runs neither does not maintain them
+    const bool need_fb = g->dir_mode != 0 || g->bitmap_div > 0;
+    for (int f = 0; f < 3; ++f) P.fb[f] = need_fb ? ws->fb[f] : nullptr;
     P.nnz = g->nnz;
     P.bu_limit = g->relabelled ? g->n_nonzero : g->n;
     P.dir_mode = g->dir_mode;
