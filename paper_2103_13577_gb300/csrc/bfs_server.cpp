@@ -140,18 +140,21 @@ static bool try_launch(bfs_server* s) {
             q.front()->launch_ns = t_launch;
             q.pop_front();
         }
-        // a share of the persistent grid so that launches on other slots
-        // can be resident at the same time
+        // with other launches in flight, a share of the persistent grid so
+        // that they stay resident together; alone, the whole grid
         L.plain = plain;
+        const bool alone = s->inflight.empty();
         if (plain) {
             const int32_t share =
-                std::max<int32_t>(s->ctx->sms, plain_grid_of(g) / (int32_t)s->slots.size());
+                alone ? plain_grid_of(g)
+                      : std::max<int32_t>(s->ctx->sms, plain_grid_of(g) / (int32_t)s->slots.size());
             for (int i = 0; i < k && st == BFS_OK; ++i)
                 st = run_plain_on(g, ws, roots[i], static_cast<int32_t*>(d_dist) + (size_t)i * g->n,
                                   nullptr, sl.stream, 0, share);
         } else {
             const int32_t share =
-                std::max<int32_t>(s->ctx->sms, g->grid_batch / (int32_t)s->slots.size());
+                alone ? g->grid_batch
+                      : std::max<int32_t>(s->ctx->sms, g->grid_batch / (int32_t)s->slots.size());
             st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, 0, share);
         }
         if (st == BFS_OK) {

@@ -353,3 +353,51 @@ def test_chunk_sizes_must_be_powers_of_two(ctx, kron16):
             g.set_bins(*bins)
     g.set_bins(32, 4096, 256, 1024)
     g.close()
+
+
+def test_l2_prefetch_option(ctx, kron16):
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col)
+    g.set_option(bfs.BFS_OPT_L2_PREFETCH, 1)
+    for bins in (None, (1, 2, 1024, 1024), (1, 1 << 20, 128, 8192)):
+        if bins:
+            g.set_bins(*bins)
+        for r in roots[:4]:
+            dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+            assert_parity(off, col, int(r), dist, parent, st)
+    with pytest.raises(bfs.BfsError):
+        g.set_option(bfs.BFS_OPT_L2_PREFETCH, 2)
+    g.close()
+
+
+def test_level_timeline(ctx, kron16):
+    """The timeline stamps init, seed and every level in order; levels match."""
+    off, col, roots = kron16
+    n = len(off) - 1
+    g = bfs.Graph(ctx, off, col)
+    stamps = torch.zeros(64, dtype=torch.int64, device="cuda")
+    bfs.bfs_debug_set_timeline(g.handle, stamps)
+    dist, parent, st = run_gpu(g, n, int(roots[0]))
+    assert_parity(off, col, int(roots[0]), dist, parent, st)
+    t = stamps.cpu().numpy()
+    k = 3 + st["levels"]
+    assert np.all(t[:k] > 0) and np.all(np.diff(t[:k]) >= 0)
+    assert np.all(t[k:] == 0)
+    # batched: [3 + 2L] after the expansion, [4 + 2L] after the sweep of level L
+    stamps.zero_()
+    rts = np.asarray(roots[:8], dtype=np.int32)
+    d = torch.empty((len(rts), n), dtype=torch.int32, device="cuda")
+    g.run_batch(rts, d)
+    bst = g.batch_sync()
+    t = stamps.cpu().numpy()
+    kb = 3 + 2 * (bst["levels"] - 1)
+    assert np.all(t[:kb] > 0) and np.all(np.diff(t[:kb]) >= 0)
+    bfs.bfs_debug_set_timeline(g.handle, None)
+    stamps.zero_()
+    run_gpu(g, n, int(roots[1]))
+    assert np.all(stamps.cpu().numpy() == 0)
+    with pytest.raises(bfs.BfsError):
+        bfs.bfs_debug_set_timeline(g.handle, torch.zeros(2, dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        bfs.bfs_debug_set_timeline(g.handle, torch.zeros(8, dtype=torch.int64))
+    g.close()
