@@ -54,6 +54,12 @@ def env_int(name, default):
         return default
 
 
+def trimmed_mean(x, cut):
+    x = np.sort(np.asarray(x, dtype=np.float64))
+    k = int(len(x) * cut)
+    return float(x[k:len(x) - k].mean()) if len(x) > 2 * k else float(x.mean())
+
+
 def hmean(x):
     x = np.asarray(x, dtype=np.float64)
     return float(len(x) / np.sum(1.0 / x))
@@ -161,6 +167,30 @@ def run_oracle_sample(off, col, roots, budget_s):
         if time.perf_counter() - t_start > budget_s:
             break
     return gteps, used
+
+
+def run_oracle_parallel(off, col, roots, budget_s):
+    """The serial oracle on distinct roots, one per host core at a time (the
+    oracle is C called through ctypes, which releases the GIL): whole-run
+    throughput in GTEPS, the roots used and the thread count."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    cores = max(1, os.cpu_count() or 1)
+    done_m, used = 0, []
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        i = 0
+        while i < len(roots):
+            batch = [int(r) for r in roots[i:i + cores]]
+            for _, _, info in ex.map(lambda r: oracle.bfs(off, col, r), batch):
+                done_m += info["edges_scanned"]
+            used += batch
+            i += cores
+            if time.perf_counter() - t0 > budget_s:
+                break
+    dt = time.perf_counter() - t0
+    return done_m / dt / 1e9, used, cores
 
 
 def reference_arm(args, rank, world):
@@ -362,6 +392,10 @@ def gpu_arm(args, rank, world, local_rank):
         gts, used = run_oracle_sample(off, col, roots, args.cpu_budget)
         cpu = {"value": hmean(gts), "unit": "GTEPS", "cores": 1, "kind": "oracle",
                "sample": f"{len(used)} of the 64 roots, serial FIFO BFS on one host core"}
+        par, pused, pcores = run_oracle_parallel(off, col, roots, args.cpu_budget)
+        cpu["all_cores"] = {"value": par, "unit": "GTEPS", "cores": pcores,
+                            "sample": f"{len(pused)} of the 64 roots, one serial BFS per core "
+                                      "at a time; sum of m_c over wall time"}
 
     if rank == 0:
         info = g.info()
@@ -380,6 +414,13 @@ def gpu_arm(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (column array %.0f MB > 129 MB)" % (len(col) * 4 / 1e6),
                        "parallelism": f"replicas x{world}"},
             "aggregate_gteps": float(m_job.sum() / (t_job.sum() * 1e-3) / 1e9),
+            "conventions": {
+                "trimmed_mean_gteps": trimmed_mean(m_job / (t_job * 1e-3) / 1e9, 0.1),
+                "paper_m_over_t_hmean": hmean(world * len(col) / (t_job * 1e-3) / 1e9),
+                "graph500_half_m_c_hmean": value / 2.0,
+                "note": "trimmed mean drops the fastest and slowest 10 % of roots; paper "
+                        "convention divides the graph's directed entries M by t; Graph500 "
+                        "counts undirected edges, m_c / 2"},
             "root_ms_median": float(np.median(t_job)),
             "e2e": {"value": e2e_value, "unit": "GTEPS", "h2d_bytes_per_step": 4 * NROOTS,
                     "d2h_bytes_per_step": 2 * 4 * n * NROOTS},
