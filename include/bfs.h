@@ -158,7 +158,15 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *                            vertex requests that vertex's column segment
  *                            (bin 2: its first 32 KiB, the rest 32 KiB ahead
  *                            of the reads), so the segment's reads find it in
- *                            L2 instead of each waiting on HBM.  Default 0. */
+ *                            L2 instead of each waiting on HBM.  Default 0.
+ *   BFS_OPT_TMA_STAGE        0/1: heavy vertices' column runs (bin 2) are
+ *                            staged in shared memory: each warp streams its
+ *                            256-entry blocks of a run through two 1 KB
+ *                            buffers filled by TMA bulk copies
+ *                            (cp.async.bulk, completion on an mbarrier), the
+ *                            next block in flight while the current one is
+ *                            probed.  Costs 16 KB of shared memory per CTA.
+ *                            Default 0. */
 #define BFS_OPT_WARP_AGGREGATE  1
 #define BFS_OPT_TIMEOUT_NS      2
 #define BFS_OPT_CTAS_PER_SM     3
@@ -169,6 +177,7 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
 #define BFS_OPT_DO_BETA         8
 #define BFS_OPT_BITMAP_FRONTIER 9
 #define BFS_OPT_L2_PREFETCH     10
+#define BFS_OPT_TMA_STAGE       11
 bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value);
 
 /* ---- autotuning -----------------------------------------------------------------

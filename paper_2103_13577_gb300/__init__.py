@@ -31,6 +31,7 @@ from ._lib import (  # noqa: F401
     BFS_OPT_HOT_MIN_EDGES,
     BFS_OPT_HOT_WORDS,
     BFS_OPT_L2_PREFETCH,
+    BFS_OPT_TMA_STAGE,
     BFS_OPT_TIMEOUT_NS,
     BFS_OPT_WARP_AGGREGATE,
     BFS_OK,

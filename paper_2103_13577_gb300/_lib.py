@@ -40,6 +40,7 @@ BFS_OPT_DO_ALPHA = 7
 BFS_OPT_DO_BETA = 8
 BFS_OPT_BITMAP_FRONTIER = 9
 BFS_OPT_L2_PREFETCH = 10
+BFS_OPT_TMA_STAGE = 11
 
 
 class BfsError(RuntimeError):

@@ -14,8 +14,8 @@
 namespace bfs {
 
 // kernels and launch helpers (bfs_kernels.cu)
-const void* plain_persistent_fn(int mb);
-const void* plain_step_fn(int mb);
+const void* plain_persistent_fn(int mb, bool staged = false);
+const void* plain_step_fn(int mb, bool staged = false);
 const void* batch_persistent_fn(int mb);
 const void* batch_step_fn(int mb);
 cudaError_t launch_csr_check(const int64_t* off, const int32_t* col, long long n, long long nnz,
@@ -268,11 +268,18 @@ static void fill_params(bfs_graph* g, Workspace* ws, TraversalParams& P) {
     // heavier vertex; the bins' counts give where it starts
     P.bitmap_from = g->relabelled ? (long long)(g->bin_count[1] + g->bin_count[2]) : 0;
     P.l2_prefetch = g->l2_prefetch;
+    P.tma_stage = g->tma_stage;
+    P.tma_offset = (int32_t)(((size_t)g->hot_words * 4 + 127) & ~(size_t)127);
     P.timeline = reinterpret_cast<unsigned long long*>(g->timeline);
     P.timeline_cap = g->timeline ? g->timeline_cap : 0;
 }
 
-static size_t plain_smem(const bfs_graph* g) { return (size_t)g->hot_words * 4; }
+// Dynamic shared memory of the plain kernels: the hot bitmap prefix, then
+// (with BFS_OPT_TMA_STAGE) two 1 KB staging buffers per warp.
+static size_t plain_smem(const bfs_graph* g) {
+    const size_t hot = ((size_t)g->hot_words * 4 + 127) & ~(size_t)127;
+    return g->tma_stage ? hot + (size_t)kWarps * 2 * 1024 : (size_t)g->hot_words * 4;
+}
 
 static bfs_status grid_size(bfs_graph* g, const void* fn, int32_t* out, size_t smem = 0) {
     int nb = 0;
@@ -294,9 +301,9 @@ static bfs_status grid_size(bfs_graph* g, const void* fn, int32_t* out, size_t s
 static bfs_status set_plain_grids(bfs_graph* g) {
     const size_t smem = plain_smem(g);
     int32_t grid2 = 0;
-    bfs_status st = grid_size(g, plain_step_fn(g->min_blocks), &grid2, smem);
+    bfs_status st = grid_size(g, plain_step_fn(g->min_blocks, g->tma_stage != 0), &grid2, smem);
     if (st != BFS_OK) return st;
-    return grid_size(g, plain_persistent_fn(g->min_blocks), &g->grid_plain, smem);
+    return grid_size(g, plain_persistent_fn(g->min_blocks, g->tma_stage != 0), &g->grid_plain, smem);
 }
 
 static bfs_status dev_status(int s) {
@@ -346,11 +353,11 @@ bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist
     P.root_caller = root;
     const size_t smem = plain_smem(g);
     if (!(flags & BFS_HOST_LOOP))
-        return launch_coop(plain_persistent_fn(g->min_blocks), grid > 0 ? grid : g->grid_plain, P,
+        return launch_coop(plain_persistent_fn(g->min_blocks, g->tma_stage != 0), grid > 0 ? grid : g->grid_plain, P,
                            s, smem);
     // host-driven level loop: init, seed, then one launch per level
     bfs_status st;
-    const void* fn = plain_step_fn(g->min_blocks);
+    const void* fn = plain_step_fn(g->min_blocks, g->tma_stage != 0);
     P.phase = 0;
     if ((st = launch_plain_kernel(fn, g->grid_plain, P, s, smem)) != BFS_OK) return st;
     P.phase = 1;
@@ -848,6 +855,17 @@ bfs_status bfs_graph_set_option(bfs_graph* g, int32_t option, int64_t value) {
         if (value < 0 || value > 1) return fail(BFS_ERR_INVALID_ARG, "must be 0 or 1");
         g->l2_prefetch = (int32_t)value;
         return BFS_OK;
+    case BFS_OPT_TMA_STAGE: {
+        if (value < 0 || value > 1) return fail(BFS_ERR_INVALID_ARG, "must be 0 or 1");
+        const int32_t old = g->tma_stage;
+        g->tma_stage = (int32_t)value;
+        bfs_status st = set_plain_grids(g);
+        if (st != BFS_OK) {
+            g->tma_stage = old;
+            set_plain_grids(g);
+        }
+        return st;
+    }
     case BFS_OPT_BITMAP_FRONTIER:
         if (value < 0 || value > (1 << 20)) return fail(BFS_ERR_INVALID_ARG, "must be in [0, 2^20]");
         g->bitmap_div = (int32_t)value;

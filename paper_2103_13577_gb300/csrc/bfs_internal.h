@@ -103,6 +103,8 @@ struct TraversalParams {
                               // vertices walk the frontier bitmap (0: never)
     long long bitmap_from;    // first vertex that can be light (degree-ordered graphs)
     int32_t l2_prefetch;      // bulk L2 prefetch of the heavy bins' column segments
+    int32_t tma_stage;        // bin-2 column blocks staged in shared memory by TMA bulk copies
+    int32_t tma_offset;       // byte offset of the staging buffers in dynamic shared memory
     int32_t timeline_cap;     // entries of timeline
     unsigned long long* timeline;  // nullable: %globaltimer after init, seed and each level
 };

@@ -96,6 +96,50 @@ __device__ __forceinline__ void stamp(const TraversalParams& P, int i) {
         P.timeline[i] = global_timer_ns();
 }
 
+// ------------------------------------------------- TMA bulk copies (1D)
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+// Arrive on bar and expect `bytes` of asynchronous transfers in this phase.
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}"
+                 ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// One bulk copy global -> shared (16-byte aligned ends, size a multiple of
+// 16), completing `bytes` transactions on bar.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, unsigned bytes,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Waits for phase `parity` of bar, giving up after the traversal's wait
+// limit (%globaltimer) or when another CTA has aborted the launch.
+__device__ __forceinline__ bool mbar_wait_bounded(const TraversalParams& P,
+                                                  unsigned long long* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_timer_ns();
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 15u) {
+            if (global_timer_ns() - t0 > (unsigned long long)P.timeout_ns) return false;
+            if (ld_volatile_i32(&P.stats->abort) != 0) return false;
+        }
+    }
+}
+
 // ------------------------------------------------------------ grid barrier
 // All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA
 // arrives on a counter; the last arrival resets it and bumps a generation
@@ -185,6 +229,10 @@ struct Stage {
     const uint32_t* hot;                               // plain: shared copy of visited[0, hot_bits)
     int hot_bits;                                      // 0 when the copy is off for this level
     int disc;                                          // plain: vertices this warp claimed
+    uint4* tma_buf;                  // plain, BFS_OPT_TMA_STAGE: two 1 KB staging buffers
+    unsigned long long* tma_bar;     // their mbarriers
+    unsigned tma_ph;                 // bit b: parity of buffer b's next phase
+    int tma_ok;                      // 0 after a staging wait gave up
 };
 
 // Warp-collective flush of the staged entries into the next frontier.
@@ -403,6 +451,31 @@ __device__ __forceinline__ void stage_init(Stage<kBatch>& S) {
         S.hot = nullptr;
         S.hot_bits = 0;
         S.disc = 0;
+        S.tma_buf = nullptr;
+        S.tma_bar = nullptr;
+        S.tma_ph = 0u;
+        S.tma_ok = 0;
+    }
+    __syncwarp();
+}
+
+// Staging buffers and mbarriers of this warp (plain kernels with
+// BFS_OPT_TMA_STAGE): two 1 KB buffers in dynamic shared memory after the
+// hot bitmap prefix, two mbarriers with one arrival per phase.
+__device__ void tma_setup(const TraversalParams& P, Stage<false>& S, uint4* s_dyn) {
+    __shared__ __align__(8) unsigned long long s_tma_bar[kWarps * 2];
+    if (!P.tma_stage) return;
+    const int warp = threadIdx.x >> 5;
+    if (lane_id() == 0) {
+        unsigned long long* bar = s_tma_bar + 2 * warp;
+        mbar_init(bar, 1u);
+        mbar_init(bar + 1, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        S.tma_buf = s_dyn + P.tma_offset / 16 + warp * 128;
+        S.tma_bar = bar;
+        S.tma_ph = 0u;
+        S.tma_ok = 1;
     }
     __syncwarp();
 }
@@ -527,12 +600,85 @@ __device__ __forceinline__ void visit_k(const TraversalParams& P, Stage<kBatch>&
 }
 
 // ------------------------------------------------------------ expansion
+// A heavy vertex's column run read through shared memory (BFS_OPT_TMA_STAGE):
+// the warp's 256-entry blocks of the run (block j at wbase + 2048 j
+// entries from a4, as in the CTA-interleaved schedule below) stream through
+// its two 1 KB buffers, each filled by one TMA bulk copy that lane 0 issues
+// two blocks ahead, so the next block is in flight while the current one is
+// probed.  valid entries: [lo, hi) relative to a4 (16-byte aligned).
+__device__ void expand_segment_staged(const TraversalParams& P, Stage<false>& S, long long a4,
+                                      int lo, int hi, int32_t v, int level, int nxt, int nslot,
+                                      int wbase) {
+    const unsigned lane = lane_id();
+    const int nblk = wbase < hi ? (hi - wbase + 2047) / 2048 : 0;
+    if (nblk == 0 || !S.tma_ok) return;
+    uint4* const buf = S.tma_buf;
+    unsigned long long* const bar = S.tma_bar;
+    unsigned ph = S.tma_ph;
+    const int32_t* const colp = P.col + a4;
+    auto issue = [&](int j) {  // lane 0
+        const int rw = wbase + j * 2048;
+        const int cnt = min(256, hi - rw);
+        const unsigned bytes = (unsigned)((cnt * 4 + 15) & ~15);
+        const int b = j & 1;
+        // the buffer's previous contents were read by the generic proxy
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(bar + b, bytes);
+        tma_load_1d(buf + b * 64, colp + rw, bytes, bar + b);
+    };
+    if (lane == 0) {
+        issue(0);
+        if (nblk > 1) issue(1);
+    }
+    int j = 0;
+    bool ok = true;
+    for (; j < nblk; ++j) {
+        const int b = j & 1;
+        ok = __all_sync(FULL_MASK, mbar_wait_bounded(P, bar + b, (ph >> b) & 1u));
+        if (!ok) break;
+        ph ^= 1u << b;
+        const uint4 x0 = buf[b * 64 + lane], x1 = buf[b * 64 + 32 + lane];
+        __syncwarp();
+        if (lane == 0 && j + 2 < nblk) issue(j + 2);
+        const int r0 = wbase + j * 2048 + 4 * (int)lane, r1 = r0 + 128;
+        unsigned okm = 0u;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (r0 + c >= lo && r0 + c < hi) okm |= 1u << c;
+            if (r1 + c >= lo && r1 + c < hi) okm |= 1u << (4 + c);
+        }
+        const int32_t u[8] = {(int32_t)x0.x, (int32_t)x0.y, (int32_t)x0.z, (int32_t)x0.w,
+                              (int32_t)x1.x, (int32_t)x1.y, (int32_t)x1.z, (int32_t)x1.w};
+        const int32_t vv[8] = {v, v, v, v, v, v, v, v};
+        visit_plain_k<8>(P, S, okm, u, vv, level, nxt, nslot);
+    }
+    if (!ok) {
+        // a copy did not land in time: stop the launch, then let the copies
+        // still in flight (blocks j and j + 1) complete before leaving
+        if (lane == 0) {
+            raise_status(P, kDevTimeout);
+            atomicExch(&P.stats->abort, 1);
+            for (int k = j; k < min(j + 2, nblk); ++k) {
+                const int b = k & 1;
+                const unsigned long long t0 = global_timer_ns();
+                while (!mbar_try_wait(bar + b, (ph >> b) & 1u) &&
+                       global_timer_ns() - t0 < (unsigned long long)P.timeout_ns) {
+                }
+                ph ^= 1u << b;
+            }
+            S.tma_ok = 0;
+        }
+    }
+    if (lane == 0) S.tma_ph = ph;
+    __syncwarp();
+}
+
 // One column segment col[a, b) of vertex v, read by a group of warps with
 // 128-bit loads (start rounded down to 16 bytes; col is padded so the
 // rounded reads stay inside the allocation).  wbase/wstride place this
 // warp's 256-entry blocks; a segment that fits in 128 entries uses one
 // 128-bit load per lane.
-template <bool kBatch>
+template <bool kBatch, bool kStaged = false>
 __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<kBatch>& S,
                                                long long a, long long b, int32_t v, uint64_t mask,
                                                int level, int nxt, int nslot, long long wbase,
@@ -541,6 +687,12 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
     const long long a4 = a & ~3ll;
     const int lo = (int)(a - a4);                 // valid entries: [lo, hi) relative to a4
     const int hi = (int)(b - a4);
+    if constexpr (!kBatch && kStaged) {
+        if (S.tma_buf != nullptr && wstride == 256ll * kWarps) {
+            expand_segment_staged(P, S, a4, lo, hi, v, level, nxt, nslot, (int)wbase);
+            return;
+        }
+    }
     const int32_t* colp = P.col + a4;
     int32_t vv[8];
     uint64_t mm[8];
@@ -718,7 +870,7 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
 
 // Bin 2: one CTA per chunk of chunk_cta edges (a heavy vertex spans many
 // chunks, hence many CTAs); the CTA's warps interleave over each segment.
-template <bool kBatch>
+template <bool kBatch, bool kStaged = false>
 __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
                                  long long item, int k, long long cnt, long long E, int level,
                                  int nxt, int nslot) {
@@ -755,7 +907,7 @@ __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int
         for (int k = 0; k < nent; ++k) {
             const long long eok = s_eo[k], bk = s_base[k];
             const long long lo = max(eok, cs), hi = min(eok + (s_end[k] - bk), ce);
-            expand_segment<kBatch>(P, S, bk + (lo - eok), bk + (hi - eok), s_v[k],
+            expand_segment<kBatch, kStaged>(P, S, bk + (lo - eok), bk + (hi - eok), s_v[k],
                                    kBatch ? s_mask[kBatch ? k : 0] : 0ull, level, nxt, nslot,
                                    (long long)warp * 256, 256ll * kWarps);
         }
@@ -955,7 +1107,7 @@ __device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, lo
 // Top-down work of one level: CTA chunks of bin 2 pulled from a counter
 // (heavy vertices spread over whichever CTAs are free), then warp items
 // (bin 1 chunks, bin 0 groups) dealt round robin over all warps of the grid.
-template <bool kBatch>
+template <bool kBatch, bool kStaged = false>
 __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
                                 int level, bool bitmap = false) {
     __shared__ long long s_item;
@@ -969,7 +1121,7 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
             const long long item = s_item;
             __syncthreads();
             if (item >= L.n_cta) break;
-            expand_cta_chunk<kBatch>(P, S, cur, item, L.k_cta, L.cnt[2], L.edges[2], level, nxt,
+            expand_cta_chunk<kBatch, kStaged>(P, S, cur, item, L.k_cta, L.cnt[2], L.edges[2], level, nxt,
                                      nslot);
         }
     }
@@ -1000,7 +1152,7 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
     }
 }
 
-template <bool kBatch>
+template <bool kBatch, bool kStaged = false>
 __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const LevelShape& L,
                              int level, uint32_t* s_hot, int dir = 0) {
     __shared__ int s_disc;
@@ -1035,7 +1187,7 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
             bottom_up = true;
         }
     }
-    if (!bottom_up) expand_top_down<kBatch>(P, S, L, level, dir == 1);
+    if (!bottom_up) expand_top_down<kBatch, kStaged>(P, S, L, level, dir == 1);
     stage_flush<kBatch>(P, S, level, nxt, nslot);
     if (!kBatch) {
         if (lane_id() == 0 && S.disc > 0) atomicAdd(&s_disc, S.disc);
@@ -1118,7 +1270,9 @@ __device__ void book_level(const TraversalParams& P, const LevelShape& S, int le
 }
 
 // --------------------------------------------------------- plain kernels
-template <int MB>
+// kStaged: heavy runs go through the TMA staging buffers (BFS_OPT_TMA_STAGE);
+// a separate instantiation, so the default kernel carries none of that code.
+template <int MB, bool kStaged>
 __global__ void __launch_bounds__(kBlock, MB)
 bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
     extern __shared__ uint4 s_dyn[];
@@ -1126,6 +1280,7 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
     __shared__ Stage<false> s_stage[kWarps];
     Stage<false>& S = s_stage[threadIdx.x >> 5];
     stage_init(S);
+    if (kStaged) tma_setup(P, S, s_dyn);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     stamp(P, 0);
@@ -1149,7 +1304,7 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
                                                            P.bitmap_div)
                                         : 0;
                 prepare_level(P, level, dir, tid, nthreads);
-                expand_level<false>(P, S, L, level, s_hot, dir);
+                expand_level<false, kStaged>(P, S, L, level, s_hot, dir);
                 prev_bu = dir == 2;
                 if (!grid_barrier(P)) break;
                 stamp(P, 3 + level);
@@ -1160,7 +1315,7 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
 }
 
 // Host-loop variant: one launch per phase / level, no grid barrier.
-template <int MB>
+template <int MB, bool kStaged>
 __global__ void __launch_bounds__(kBlock, MB)
 bfs_plain_step(const __grid_constant__ TraversalParams P) {
     extern __shared__ uint4 s_dyn[];
@@ -1168,6 +1323,7 @@ bfs_plain_step(const __grid_constant__ TraversalParams P) {
     __shared__ Stage<false> s_stage[kWarps];
     Stage<false>& S = s_stage[threadIdx.x >> 5];
     stage_init(S);
+    if (kStaged) tma_setup(P, S, s_dyn);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     if (P.phase == 0) {
@@ -1180,7 +1336,7 @@ bfs_plain_step(const __grid_constant__ TraversalParams P) {
         if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
         const int dir = (P.fb[0] && P.dir_override > 0) ? P.dir_override : 0;
         prepare_level(P, P.level, dir, tid, nthreads);
-        expand_level<false>(P, S, L, P.level, s_hot, dir);
+        expand_level<false, kStaged>(P, S, L, P.level, s_hot, dir);
     }
 }
 
@@ -1511,13 +1667,21 @@ __global__ void degree_bins_kernel(const int64_t* off, long long n, int t_small,
 // Kernels are instantiated for 2, 3 and 4 resident CTAs per SM (register
 // cap 128, 80 or 64; batched kernels 2 and 3); the graph's occupancy option
 // picks one.
-const void* plain_persistent_fn(int mb) {
-    return mb >= 4 ? (const void*)bfs_plain_persistent<4>
-         : mb == 3 ? (const void*)bfs_plain_persistent<3> : (const void*)bfs_plain_persistent<2>;
+const void* plain_persistent_fn(int mb, bool staged) {
+    if (staged)
+        return mb >= 4 ? (const void*)bfs_plain_persistent<4, true>
+             : mb == 3 ? (const void*)bfs_plain_persistent<3, true>
+                       : (const void*)bfs_plain_persistent<2, true>;
+    return mb >= 4 ? (const void*)bfs_plain_persistent<4, false>
+         : mb == 3 ? (const void*)bfs_plain_persistent<3, false>
+                   : (const void*)bfs_plain_persistent<2, false>;
 }
-const void* plain_step_fn(int mb) {
-    return mb >= 4 ? (const void*)bfs_plain_step<4>
-         : mb == 3 ? (const void*)bfs_plain_step<3> : (const void*)bfs_plain_step<2>;
+const void* plain_step_fn(int mb, bool staged) {
+    if (staged)
+        return mb >= 4 ? (const void*)bfs_plain_step<4, true>
+             : mb == 3 ? (const void*)bfs_plain_step<3, true> : (const void*)bfs_plain_step<2, true>;
+    return mb >= 4 ? (const void*)bfs_plain_step<4, false>
+         : mb == 3 ? (const void*)bfs_plain_step<3, false> : (const void*)bfs_plain_step<2, false>;
 }
 const void* batch_persistent_fn(int mb) {
     return mb >= 3 ? (const void*)bfs_batch_persistent<3> : (const void*)bfs_batch_persistent<2>;

@@ -90,6 +90,7 @@ struct bfs_graph {
     int32_t do_alpha = 15, do_beta = 18;
     int32_t bitmap_div = 0;           // bitmap top-down when frontier > n / bitmap_div
     int32_t l2_prefetch = 0;          // bulk L2 prefetch of bin 1 / bin 2 column segments
+    int32_t tma_stage = 0;            // bin-2 blocks staged in shared memory by TMA
     uint64_t* timeline = nullptr;     // diagnostics: device array of level timestamps
     int32_t timeline_cap = 0;
     int64_t n_nonzero = 0;            // vertices with out-degree > 0

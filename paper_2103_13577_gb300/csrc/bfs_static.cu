@@ -17,7 +17,7 @@
 
 namespace bfs {
 
-const void* plain_persistent_fn(int mb);
+const void* plain_persistent_fn(int mb, bool staged = false);
 
 namespace {
 

@@ -401,3 +401,25 @@ def test_level_timeline(ctx, kron16):
     with pytest.raises(ValueError):
         bfs.bfs_debug_set_timeline(g.handle, torch.zeros(8, dtype=torch.int64))
     g.close()
+
+
+@pytest.mark.parametrize("bins", [None, (1, 2, 1024, 1024), (4, 64, 128, 2048)])
+def test_tma_staged_heavy_runs(ctx, kron16, bins):
+    """Bin-2 column runs staged in shared memory by TMA bulk copies: same
+    distances and valid parents, single-source and host-loop."""
+    off, col, roots = kron16
+    g = bfs.Graph(ctx, off, col)
+    if bins:
+        g.set_bins(*bins)
+    g.set_option(bfs.BFS_OPT_TMA_STAGE, 1)
+    for r in roots[:6]:
+        dist, parent, st = run_gpu(g, len(off) - 1, int(r))
+        assert_parity(off, col, int(r), dist, parent, st)
+    dist, parent, st = run_gpu(g, len(off) - 1, int(roots[0]), flags=bfs.BFS_HOST_LOOP)
+    assert_parity(off, col, int(roots[0]), dist, parent, st)
+    g.set_option(bfs.BFS_OPT_DIRECTION, 1)
+    dist, parent, st = run_gpu(g, len(off) - 1, int(roots[1]))
+    assert_parity(off, col, int(roots[1]), dist, parent, st)
+    with pytest.raises(bfs.BfsError):
+        g.set_option(bfs.BFS_OPT_TMA_STAGE, 3)
+    g.close()
