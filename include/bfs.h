@@ -67,6 +67,13 @@ typedef int64_t bfs_ticket;
 #define BFS_DIST_INT8           0x2u  /* bfs_run_batch: int8 distances (levels <= 126) */
 #define BFS_HOST_LOOP           0x4u  /* one kernel launch per level, host reads the frontier
                                          size between levels (no device-side loop) */
+#define BFS_GRAPH_LOOP          0x8u  /* the level loop as a CUDA graph: init, seed, then a
+                                         conditional while node whose body (the level's
+                                         kernels and a one-CTA step that sets the condition
+                                         from the next frontier's size) repeats on the device;
+                                         no cooperative launch, no host round trip.  The
+                                         instantiated graph is kept per graph and output
+                                         buffers and reused with new roots. */
 
 /* ---- context ------------------------------------------------------------
  * A context binds the library to one CUDA device.  arena (device pointer,

@@ -22,6 +22,7 @@ from ._lib import (  # noqa: F401
     BFS_ERR_ROOT_RANGE,
     BFS_ERR_TIMEOUT,
     BFS_ERR_UNSUPPORTED,
+    BFS_GRAPH_LOOP,
     BFS_HOST_LOOP,
     BFS_OPT_BITMAP_FRONTIER,
     BFS_OPT_CTAS_PER_SM,

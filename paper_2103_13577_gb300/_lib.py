@@ -29,6 +29,7 @@ BFS_UPLOAD_NO_RELABEL = 0x2
 BFS_OUT_HOST = 0x1
 BFS_DIST_INT8 = 0x2
 BFS_HOST_LOOP = 0x4
+BFS_GRAPH_LOOP = 0x8
 BFS_TUNE_BATCHED = 0x1
 BFS_OPT_WARP_AGGREGATE = 1
 BFS_OPT_TIMEOUT_NS = 2

@@ -344,6 +344,119 @@ static bool ctl_empty(const LevelCtl& c) {
            0;
 }
 
+// ------------------------------------------- graph-captured level loop
+// One instantiated CUDA graph per graph and kind (single-source, batched):
+// init -> seed -> while(cond) { level kernels -> one-CTA step that sets
+// cond } [-> emit].  The key is the launch parameters without the per-run
+// fields; when a run's key matches, only the seed node's parameters (the
+// roots) are updated before the launch, otherwise the graph is rebuilt.
+struct GraphLoop {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t seed = nullptr;
+    cudaGraphConditionalHandle cond = 0;
+    const void* fn = nullptr;
+    size_t smem = 0;
+    TraversalParams key;
+};
+
+void graph_loop_free(GraphLoop*& gl) {
+    if (!gl) return;
+    if (gl->exec) cudaGraphExecDestroy(gl->exec);
+    if (gl->graph) cudaGraphDestroy(gl->graph);
+    delete gl;
+    gl = nullptr;
+}
+
+static TraversalParams graph_key(const TraversalParams& P) {
+    TraversalParams k;
+    std::memcpy(&k, &P, sizeof(k));
+    k.root_caller = 0;
+    std::memset(k.roots, 0, sizeof(k.roots));
+    k.phase = 0;
+    k.level = 0;
+    k.graph_cond = 0;
+    return k;
+}
+
+static cudaError_t add_step_node(cudaGraphNode_t* out, cudaGraph_t gr, const cudaGraphNode_t* dep,
+                                 const void* fn, const TraversalParams& P, int phase, int blocks,
+                                 size_t smem) {
+    TraversalParams Q;
+    std::memcpy(&Q, &P, sizeof(Q));
+    Q.phase = phase;
+    void* args[] = {&Q};
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = dim3((unsigned)blocks);
+    kp.blockDim = dim3(kBlock);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    return cudaGraphAddKernelNode(out, gr, dep, dep ? 1 : 0, &kp);
+}
+
+static bfs_status launch_graph_loop(GraphLoop*& gl, TraversalParams P, const void* fn, bool batched,
+                                    int32_t grid, size_t smem, cudaStream_t s) {
+    const TraversalParams key = graph_key(P);
+    cudaError_t e = cudaSuccess;
+    if (gl && gl->fn == fn && gl->smem == smem && std::memcmp(&gl->key, &key, sizeof(key)) == 0) {
+        TraversalParams Q;
+        std::memcpy(&Q, &P, sizeof(Q));
+        Q.phase = 1;
+        Q.graph_cond = gl->cond;
+        void* args[] = {&Q};
+        cudaKernelNodeParams kp = {};
+        kp.func = const_cast<void*>(fn);
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(kBlock);
+        kp.sharedMemBytes = (unsigned)smem;
+        kp.kernelParams = args;
+        e = cudaGraphExecKernelNodeSetParams(gl->exec, gl->seed, &kp);
+        if (e == cudaSuccess) e = cudaGraphLaunch(gl->exec, s);
+        return e == cudaSuccess ? BFS_OK : cuda_fail(e, "graph loop launch");
+    }
+    graph_loop_free(gl);
+    gl = new (std::nothrow) GraphLoop();
+    if (!gl) return fail(BFS_ERR_NO_MEMORY, "host allocation failed");
+    gl->fn = fn;
+    gl->smem = smem;
+    std::memcpy(&gl->key, &key, sizeof(key));
+    cudaGraphNode_t n_init = nullptr, n_while = nullptr, b1 = nullptr, b2 = nullptr, b3 = nullptr;
+    cudaGraphNode_t n_emit = nullptr;
+    e = cudaGraphCreate(&gl->graph, 0);
+    if (e == cudaSuccess)
+        e = cudaGraphConditionalHandleCreate(&gl->cond, gl->graph, 1u, cudaGraphCondAssignDefault);
+    P.graph_cond = gl->cond;
+    if (e == cudaSuccess) e = add_step_node(&n_init, gl->graph, nullptr, fn, P, 0, grid, smem);
+    if (e == cudaSuccess) e = add_step_node(&gl->seed, gl->graph, &n_init, fn, P, 1, 1, smem);
+    cudaGraph_t body = nullptr;
+    if (e == cudaSuccess) {
+        cudaGraphNodeParams cp = {};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = gl->cond;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&n_while, gl->graph, &gl->seed, nullptr, 1, &cp);
+        if (e == cudaSuccess) body = cp.conditional.phGraph_out[0];
+    }
+    if (!batched) {
+        if (e == cudaSuccess) e = add_step_node(&b1, body, nullptr, fn, P, 5, grid, smem);
+        if (e == cudaSuccess) e = add_step_node(&b2, body, &b1, fn, P, 6, 1, smem);
+    } else {
+        if (e == cudaSuccess) e = add_step_node(&b1, body, nullptr, fn, P, 7, grid, smem);
+        if (e == cudaSuccess) e = add_step_node(&b2, body, &b1, fn, P, 8, grid, smem);
+        if (e == cudaSuccess) e = add_step_node(&b3, body, &b2, fn, P, 9, 1, smem);
+        if (e == cudaSuccess) e = add_step_node(&n_emit, gl->graph, &n_while, fn, P, 4, grid, smem);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&gl->exec, gl->graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(gl->exec, s);
+    if (e != cudaSuccess) {
+        graph_loop_free(gl);
+        return cuda_fail(e, "graph loop");
+    }
+    return BFS_OK;
+}
+
 bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist,
                         int32_t* parent, cudaStream_t s, uint32_t flags, int32_t grid) {
     TraversalParams P;
@@ -352,9 +465,12 @@ bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist
     P.parent = parent;
     P.root_caller = root;
     const size_t smem = plain_smem(g);
+    if (flags & BFS_GRAPH_LOOP)
+        return launch_graph_loop(g->loop_plain, P, plain_step_fn(g->min_blocks, g->tma_stage != 0),
+                                 false, grid > 0 ? grid : g->grid_plain, smem, s);
     if (!(flags & BFS_HOST_LOOP))
-        return launch_coop(plain_persistent_fn(g->min_blocks, g->tma_stage != 0), grid > 0 ? grid : g->grid_plain, P,
-                           s, smem);
+        return launch_coop(plain_persistent_fn(g->min_blocks, g->tma_stage != 0),
+                           grid > 0 ? grid : g->grid_plain, P, s, smem);
     // host-driven level loop: init, seed, then one launch per level
     bfs_status st;
     const void* fn = plain_step_fn(g->min_blocks, g->tma_stage != 0);
@@ -398,6 +514,8 @@ bfs_status run_batch_on(bfs_graph* g, Workspace* ws, const int32_t* roots, int32
     P.dist_int8 = (flags & BFS_DIST_INT8) ? 1 : 0;
     for (int i = 0; i < k; ++i) P.roots[i] = roots[i];
     P.dist = static_cast<int32_t*>(dist);
+    if (flags & BFS_GRAPH_LOOP)
+        return launch_graph_loop(g->loop_batch, P, batch_step_fn(g->min_blocks), true, grid, 0, s);
     if (!(flags & BFS_HOST_LOOP)) return launch_coop(batch_persistent_fn(g->min_blocks), grid, P, s);
     bfs_status st;
     P.phase = 0;
@@ -673,6 +791,8 @@ bfs_status bfs_graph_free(bfs_graph* g) {
     cudaSetDevice(g->ctx->device);
     cudaDeviceSynchronize();
     DeviceAllocator* m = g->ctx->mem;
+    graph_loop_free(g->loop_plain);
+    graph_loop_free(g->loop_batch);
     free_workspace(g, g->ws_plain);
     free_workspace(g, g->ws_batch);
     m->release(g->d_off);
@@ -731,7 +851,10 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large, in
 bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* dist, int32_t* parent, void* stream,
                    uint32_t flags) {
     if (!g || !dist) return fail(BFS_ERR_INVALID_ARG, "null graph or dist");
-    if (flags & ~(BFS_OUT_HOST | BFS_HOST_LOOP)) return fail(BFS_ERR_INVALID_ARG, "unknown flag");
+    if (flags & ~(BFS_OUT_HOST | BFS_HOST_LOOP | BFS_GRAPH_LOOP))
+        return fail(BFS_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & BFS_HOST_LOOP) && (flags & BFS_GRAPH_LOOP))
+        return fail(BFS_ERR_INVALID_ARG, "BFS_HOST_LOOP and BFS_GRAPH_LOOP are exclusive");
     if (root < 0 || root >= g->n) return fail(BFS_ERR_ROOT_RANGE, "root out of range");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(g->mu);
@@ -773,8 +896,10 @@ bfs_status bfs_run_batch(bfs_graph* g, const int32_t* roots, int32_t k, void* di
                          uint32_t flags) {
     if (!g || !roots || !dist) return fail(BFS_ERR_INVALID_ARG, "null argument");
     if (k < 1 || k > 64) return fail(BFS_ERR_INVALID_ARG, "k must be in 1..64");
-    if (flags & ~(BFS_OUT_HOST | BFS_DIST_INT8 | BFS_HOST_LOOP))
+    if (flags & ~(BFS_OUT_HOST | BFS_DIST_INT8 | BFS_HOST_LOOP | BFS_GRAPH_LOOP))
         return fail(BFS_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & BFS_HOST_LOOP) && (flags & BFS_GRAPH_LOOP))
+        return fail(BFS_ERR_INVALID_ARG, "BFS_HOST_LOOP and BFS_GRAPH_LOOP are exclusive");
     for (int i = 0; i < k; ++i)
         if (roots[i] < 0 || roots[i] >= g->n) return fail(BFS_ERR_ROOT_RANGE, "root out of range");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -43,6 +43,13 @@ struct DevStats {
     int abort;        // set with status; tells waiting CTAs to leave; cleared at kernel exit
     int bu_levels;    // levels run bottom-up
     int pad[2];
+    // graph-captured level loop: the state the device-side loop keeps in
+    // registers, carried between the loop body's launches
+    long long graph_seen;  // edges of all frontiers so far
+    int graph_level;       // level the next body launch expands
+    int graph_prev_bu;     // the previous level ran bottom-up
+    int graph_dir;         // direction of the level just expanded
+    int graph_pad;
 };
 
 // Frontier queue of one bin (one of two ping-pong copies).
@@ -107,6 +114,7 @@ struct TraversalParams {
     int32_t tma_offset;       // byte offset of the staging buffers in dynamic shared memory
     int32_t timeline_cap;     // entries of timeline
     unsigned long long* timeline;  // nullable: %globaltimer after init, seed and each level
+    unsigned long long graph_cond; // graph-captured loop: conditional handle of the while node
 };
 
 // Direction of level L (Beamer, Asanovic, Patterson, "Direction-optimizing

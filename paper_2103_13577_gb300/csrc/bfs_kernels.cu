@@ -1226,6 +1226,10 @@ __device__ void init_plain(const TraversalParams& P, long long tid, long long nt
         P.stats->status = 0;
         P.stats->max_level = 0;
         P.stats->bu_levels = 0;
+        P.stats->graph_seen = 0;
+        P.stats->graph_level = 0;
+        P.stats->graph_prev_bu = 0;
+        P.stats->graph_dir = 0;
     }
     const long long words = (P.n + 31) / 32;
     fill_bytes(P.visited, words * 4, 0, tid, nthreads);
@@ -1267,6 +1271,55 @@ __device__ void book_level(const TraversalParams& P, const LevelShape& S, int le
         P.stats->reached += S.discovered;
     }
     P.stats->edges += S.edges[0] + S.edges[1] + S.edges[2];
+}
+
+// ------------------------------------------- graph-captured level loop
+// End of one loop-body launch (one CTA, thread 0): carry the direction
+// state to the next level and set the while node's condition -- 0 when the
+// next frontier is empty (its discoveries of degree-0 vertices are booked
+// first, as the device-side loop does) or the launch failed.
+__device__ void graph_advance_plain(const TraversalParams& P) {
+    if (threadIdx.x != 0) return;
+    DevStats* st = P.stats;
+    const int level = st->graph_level;
+    const int slot = level % 3, nslot = (level + 1) % 3;
+    long long mf = 0, nf_next = 0;
+#pragma unroll
+    for (int b = 0; b < kBins; ++b) {
+        mf += (long long)(ld_cg_u64(&P.ctl[slot].packed[b]) & kEdgeMask);
+        nf_next += (long long)(ld_cg_u64(&P.ctl[nslot].packed[b]) >> kCountShift);
+    }
+    st->graph_seen += mf;
+    st->graph_prev_bu = st->graph_dir == 2 ? 1 : 0;
+    st->graph_level = level + 1;
+    unsigned go = 1u;
+    if (nf_next == 0 || ld_volatile_i32(&st->status) != 0) {
+        if (nf_next == 0) book_level(P, read_level(P, level + 1), level + 1);
+        go = 0u;
+    }
+    cudaGraphSetConditional(P.graph_cond, go);
+}
+
+// Batched body end: records the level count, applies the int8 depth limit
+// and sets the while node's condition for the next level.
+__device__ void graph_advance_batch(const TraversalParams& P) {
+    if (threadIdx.x != 0) return;
+    DevStats* st = P.stats;
+    const int level = st->graph_level;
+    const int nslot = (level + 1) % 3;
+    if (ld_cg_u64(reinterpret_cast<const unsigned long long*>(&P.ctl[nslot].new_lanes)) > 0ull)
+        st->levels = level + 2;
+    long long nf_next = 0;
+#pragma unroll
+    for (int b = 0; b < kBins; ++b)
+        nf_next += (long long)(ld_cg_u64(&P.ctl[nslot].packed[b]) >> kCountShift);
+    st->graph_level = level + 1;
+    unsigned go = (nf_next > 0 && ld_volatile_i32(&st->status) == 0) ? 1u : 0u;
+    if (go && P.dist_int8 && level + 2 > 126) {
+        raise_status(P, kDevDepth);
+        go = 0u;
+    }
+    cudaGraphSetConditional(P.graph_cond, go);
 }
 
 // --------------------------------------------------------- plain kernels
@@ -1330,13 +1383,33 @@ bfs_plain_step(const __grid_constant__ TraversalParams P) {
         init_plain(P, tid, nthreads);
     } else if (P.phase == 1) {
         seed_plain(P, S);
-    } else {
+    } else if (P.phase == 2) {
         const LevelShape L = read_level(P, P.level);
         book_level(P, L, P.level);
         if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
         const int dir = (P.fb[0] && P.dir_override > 0) ? P.dir_override : 0;
         prepare_level(P, P.level, dir, tid, nthreads);
         expand_level<false, kStaged>(P, S, L, P.level, s_hot, dir);
+    } else if (P.phase == 5) {
+        // graph-captured loop body: the level and the direction state come
+        // from the device (written by the previous body launch)
+        const int level = ld_volatile_i32(&P.stats->graph_level);
+        const LevelShape L = read_level(P, level);
+        book_level(P, L, level);
+        const long long nf = L.cnt[0] + L.cnt[1] + L.cnt[2];
+        if (nf == 0) return;
+        const long long mf = L.edges[0] + L.edges[1] + L.edges[2];
+        const long long seen = *(volatile long long*)&P.stats->graph_seen + mf;
+        const int dir = P.fb[0] ? choose_direction(P.dir_mode,
+                                                   ld_volatile_i32(&P.stats->graph_prev_bu) != 0,
+                                                   mf, P.nnz - seen, nf, P.n, P.do_alpha,
+                                                   P.do_beta, P.bitmap_div)
+                                : 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) P.stats->graph_dir = dir;
+        prepare_level(P, level, dir, tid, nthreads);
+        expand_level<false, kStaged>(P, S, L, level, s_hot, dir);
+    } else if (P.phase == 6) {
+        graph_advance_plain(P);
     }
 }
 
@@ -1350,6 +1423,7 @@ __device__ void init_batch(const TraversalParams& P, long long tid, long long nt
         P.stats->edges = 0;
         P.stats->status = 0;
         P.stats->max_level = 0;
+        P.stats->graph_level = 0;
     }
     fill_u64(P.lane_vn, 2 * P.n, tid, nthreads);
     // distances are not filled here: emit_batch writes every (lane, vertex)
@@ -1580,8 +1654,19 @@ bfs_batch_step(const __grid_constant__ TraversalParams P) {
         expand_level<true>(P, S, L, P.level, nullptr);
     } else if (P.phase == 3) {
         sweep_batch(P, S, P.level, tid, nthreads);
-    } else {
+    } else if (P.phase == 4) {
         emit_batch(P, tid, nthreads);
+    } else if (P.phase == 7) {
+        // graph-captured loop body: expansion of the device's current level
+        const int level = ld_volatile_i32(&P.stats->graph_level);
+        const LevelShape L = read_level(P, level);
+        if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
+        book_batch_level(P, level);
+        expand_level<true>(P, S, L, level, nullptr);
+    } else if (P.phase == 8) {
+        sweep_batch(P, S, ld_volatile_i32(&P.stats->graph_level), tid, nthreads);
+    } else if (P.phase == 9) {
+        graph_advance_batch(P);
     }
 }
 

@@ -65,7 +65,13 @@ struct bfs_context {
     bfs::DeviceAllocator* mem = nullptr;
 };
 
+namespace bfs {
+struct GraphLoop;  // an instantiated graph-captured level loop (BFS_GRAPH_LOOP)
+}
+
 struct bfs_graph {
+    bfs::GraphLoop* loop_plain = nullptr;
+    bfs::GraphLoop* loop_batch = nullptr;
     bfs_context* ctx = nullptr;
     int64_t n = 0, nnz = 0, max_degree = 0;
     int64_t* d_off = nullptr;
