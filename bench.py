@@ -380,6 +380,16 @@ def gpu_arm(args, rank, world, local_rank):
     bst = g.batch_sync(stream)
     batch_ms = bev[0].elapsed_time(bev[1]) / reps
     batch_gteps = bst["edges_scanned"] / (batch_ms * 1e-3) / 1e9
+    g.set_option(bfs.BFS_OPT_DIRECTION, 1)
+    g.run_batch(roots, bd, stream=stream)
+    g.batch_sync(stream)
+    bev[0].record(stream)
+    for _ in range(reps):
+        g.run_batch(roots, bd, stream=stream)
+    bev[1].record(stream)
+    bdo = g.batch_sync(stream)
+    g.set_option(bfs.BFS_OPT_DIRECTION, 0)
+    batch_do_ms = bev[0].elapsed_time(bev[1]) / reps
 
     # roofline of the traversal kernel (one launch per root)
     peak, peak_kind = measured_hbm_peak()
@@ -442,7 +452,11 @@ def gpu_arm(args, rank, world, local_rank):
                         "host-driven level loop (bfs_run_lrb), same roots, this rank"},
             "batched": {"roots": NROOTS, "ms": batch_ms, "gteps": batch_gteps,
                         "edges": int(bst["edges_scanned"]), "levels": int(bst["levels"]),
-                        "speedup_vs_plain_step": ms_step / batch_ms},
+                        "speedup_vs_plain_step": ms_step / batch_ms,
+                        "direction_optimizing": {
+                            "ms": batch_do_ms,
+                            "gteps": bdo["edges_scanned"] / (batch_do_ms * 1e-3) / 1e9,
+                            "bottom_up_levels": int(bdo["bottom_up_levels"])}},
             "clocks": clk,
             "gpu_launches": int(args.steps * NROOTS),
         }
@@ -502,7 +516,10 @@ def batched_arm(args):
         tune_b = g.autotune(roots, batched=True)
         rec["tuned_batched"] = {k: tune_b[k] for k in ("t_small", "t_large", "chunk_warp", "chunk_cta", "ctas_per_sm")}
         res = {}
-        for dt_name, dt in (("int32", torch.int32), ("int8", torch.int8)):
+        for dt_name, dt, direction in (("int32", torch.int32, 0), ("int8", torch.int8, 0),
+                                       ("int32_direction_optimizing", torch.int32, 1),
+                                       ("int8_direction_optimizing", torch.int8, 1)):
+            g.set_option(bfs.BFS_OPT_DIRECTION, direction)
             bd = torch.empty((NROOTS, n), dtype=dt, device="cuda")
             g.run_batch(roots, bd, stream=stream)
             bst = g.batch_sync(stream)
@@ -515,7 +532,9 @@ def batched_arm(args):
             bst = g.batch_sync(stream)
             ms = ev[0].elapsed_time(ev[1]) / reps
             res[dt_name] = {"ms": ms, "gteps": bst["edges_scanned"] / (ms * 1e-3) / 1e9,
-                            "levels": int(bst["levels"])}
+                            "levels": int(bst["levels"]),
+                            "bottom_up_levels": int(bst["bottom_up_levels"])}
+            g.set_option(bfs.BFS_OPT_DIRECTION, 0)
             del bd
         rec.update({"sum_m_c": int(m_c), "plain_64_runs_ms": plain_ms,
                     "plain_gteps_aggregate": m_c / (plain_ms * 1e-3) / 1e9,
@@ -523,7 +542,9 @@ def batched_arm(args):
                     "direction_optimizing_gteps_aggregate": m_c / (do_ms * 1e-3) / 1e9,
                     "batched": res,
                     "batched_speedup_vs_plain": plain_ms / res["int32"]["ms"],
-                    "batched_speedup_vs_direction_optimizing": do_ms / res["int32"]["ms"]})
+                    "batched_speedup_vs_direction_optimizing": do_ms / res["int32"]["ms"],
+                    "batched_direction_optimizing_speedup_vs_plain":
+                        plain_ms / res["int32_direction_optimizing"]["ms"]})
         out["graphs"].append(rec)
         g.close()
         del dist, parent

@@ -149,7 +149,12 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large,
  *                            and returns to top-down when the frontier holds
  *                            fewer than n / beta vertices.  2: bottom-up on
  *                            every level (for testing).  Distances are the
- *                            same in every mode.  Modes 1 and 2 need a
+ *                            same in every mode.  Batched runs (persistent
+ *                            and graph loops) take the same decisions with
+ *                            lane sets: a bottom-up batched level ORs the
+ *                            neighbours' frontier lane sets into each vertex
+ *                            until every lane it lacks is found; host-loop
+ *                            batched runs stay top-down.  Modes 1 and 2 need a
  *                            symmetric graph (bottom-up follows a vertex's own
  *                            adjacency); the upload tests symmetry and other
  *                            graphs refuse them with BFS_ERR_UNSUPPORTED.

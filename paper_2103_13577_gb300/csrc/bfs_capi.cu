@@ -142,7 +142,9 @@ size_t workspace_bytes(const bfs_graph* g, bool batched, int /*nlanes*/) {
         if (batched) per += round_up(cap * 8, kAlign);
         b += 2 * per;
     }
-    if (batched) b += round_up((size_t)g->n * 16, kAlign) + round_up((size_t)g->n * 64, kAlign);
+    if (batched)
+        b += round_up((size_t)g->n * 16, kAlign) + round_up((size_t)g->n * 8, kAlign) +
+             round_up((size_t)g->n * 64, kAlign);
     return b;
 }
 
@@ -165,6 +167,7 @@ void free_workspace(bfs_graph* g, Workspace* ws) {
         }
     m->release(ws->control);
     m->release(ws->lane_vn);
+    m->release(ws->lane_front);
     m->release(ws->lane_level);
     m->release(ws->dist_scratch);
     m->release(ws->parent_scratch);
@@ -208,6 +211,7 @@ Workspace* make_workspace(bfs_graph* g, DeviceAllocator* m, bool batched, cudaSt
     ws->control = static_cast<char*>(get(control_bytes()));
     if (batched) {
         ws->lane_vn = static_cast<uint64_t*>(get((size_t)g->n * 16));
+        ws->lane_front = static_cast<uint64_t*>(get((size_t)g->n * 8));
         ws->lane_level = static_cast<uint8_t*>(get((size_t)g->n * 64));
     }
     if (!ok) {
@@ -247,6 +251,7 @@ static void fill_params(bfs_graph* g, Workspace* ws, TraversalParams& P) {
     P.bar = ws->bar;
     P.stats = ws->stats;
     P.lane_vn = ws->lane_vn;
+    P.lane_front = ws->lane_front;
     P.lane_level = ws->lane_level;
     P.timeout_ns = g->timeout_ns;
     P.debug_stall = g->debug_stall;

@@ -25,7 +25,8 @@ struct LevelCtl {
     unsigned int work;                  // dynamic work-item counter of this level
     unsigned int discovered;            // vertices claimed at this level (any degree)
     unsigned long long new_lanes;       // batched: (vertex, lane) pairs discovered
-    unsigned long long pad[2];
+    unsigned long long front_lanes;     // batched: lanes with a non-empty frontier
+    unsigned long long pad[1];
 };
 
 struct GridBarrier {
@@ -50,6 +51,7 @@ struct DevStats {
     int graph_prev_bu;     // the previous level ran bottom-up
     int graph_dir;         // direction of the level just expanded
     int graph_pad;
+    long long full_edges;  // batched: degree sum of the vertices every lane has reached
 };
 
 // Frontier queue of one bin (one of two ping-pong copies).
@@ -82,6 +84,7 @@ struct TraversalParams {
     DevStats* stats;
     // batched traversal state
     uint64_t* lane_vn;        // [n][2]: lanes that reached v (visited), lanes reaching v next
+    uint64_t* lane_front;     // [n]: lanes for which v is in the current frontier
     uint8_t* lane_level;      // [n][64]: level of each lane at each vertex
     int32_t nlanes;
     int32_t dist_int8;

@@ -1007,6 +1007,90 @@ __device__ void bottom_up_level(const TraversalParams& P, Stage<false>& S, int l
     }
 }
 
+// Batched bottom-up level (a multi-source BFS over lane sets): every vertex
+// that lacks some lane whose frontier is non-empty ORs the frontier lane
+// sets of its neighbours and stops once it has every such lane.  Rows are
+// scanned two ways: a warp scans one row 32 entries per step, OR-reducing
+// the lane sets across the warp (the heavy vertices -- below `heavy_end`
+// in the degree order, one vertex per warp spread over the grid -- and any
+// heavy row met among the light ones), and a lane scans a light row four
+// entries at a time.  The lanes found go to next[v] (each vertex has one
+// owner, so no atomics) and the sweep turns them into distances and the
+// next frontier, as after a top-down level.  Frontier sets are read past
+// L1 (the previous level's sweep wrote them).
+__device__ __forceinline__ uint64_t warp_scan_row(const unsigned long long* F, const int32_t* col,
+                                                  long long k, long long e, uint64_t need) {
+    const unsigned lane = lane_id();
+    uint64_t found = 0ull;
+    for (long long kk = k; kk < e; kk += 32) {
+        uint64_t f = 0ull;
+        if (kk + lane < e) f = __ldcg(F + __ldg(col + kk + lane));
+        const unsigned lo = __reduce_or_sync(FULL_MASK, (unsigned)f);
+        const unsigned hi = __reduce_or_sync(FULL_MASK, (unsigned)(f >> 32));
+        found |= ((uint64_t)hi << 32) | lo;
+        if ((found & need) == need) break;
+    }
+    return found;
+}
+
+__device__ void bottom_up_batch_level(const TraversalParams& P, int level) {
+    const unsigned lane = lane_id();
+    // only lanes whose frontier is non-empty can be found at this level; a
+    // lane whose traversal has ended would otherwise keep every vertex it
+    // never reaches scanning its whole row
+    const uint64_t live = ld_cg_u64(&P.ctl[level % 3].front_lanes);
+    const unsigned long long* F = reinterpret_cast<const unsigned long long*>(P.lane_front);
+    unsigned long long* const vn = reinterpret_cast<unsigned long long*>(P.lane_vn);
+    const long long nwarps = (long long)gridDim.x * kWarps;
+    const long long gw = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);
+    const long long heavy_end = min(P.bitmap_from, P.bu_limit);
+    for (long long v = gw; v < heavy_end; v += nwarps) {
+        const uint64_t need = live & ~__ldcg(vn + 2 * v);
+        if (need == 0ull) continue;
+        const uint64_t found =
+            warp_scan_row(F, P.col, __ldg(P.off + v), __ldg(P.off + v + 1), need);
+        if (lane == 0 && (found & need) != 0ull) vn[2 * v + 1] = found & need;
+    }
+    const long long groups = (P.bu_limit - heavy_end + 31) / 32;
+    for (long long w = gw; w < groups; w += nwarps) {
+        const long long v = heavy_end + w * 32 + lane;
+        uint64_t need = 0ull;
+        long long k = 0, e = 0;
+        if (v < P.bu_limit) {
+            need = live & ~__ldcg(vn + 2 * v);
+            if (need != 0ull) {
+                k = __ldg(P.off + v);
+                e = __ldg(P.off + v + 1);
+            }
+        }
+        const bool heavy = e - k > 32;
+        if (__ballot_sync(FULL_MASK, need != 0ull) == 0u) continue;
+        uint64_t found = 0ull;
+        if (need != 0ull && !heavy) {
+            for (; k + 4 <= e; k += 4) {
+                const int32_t u0 = __ldg(P.col + k), u1 = __ldg(P.col + k + 1);
+                const int32_t u2 = __ldg(P.col + k + 2), u3 = __ldg(P.col + k + 3);
+                found |= __ldcg(F + u0) | __ldcg(F + u1) | __ldcg(F + u2) | __ldcg(F + u3);
+                if ((found & need) == need) break;
+            }
+            if ((found & need) != need)
+                for (; k < e; ++k) {
+                    found |= __ldcg(F + __ldg(P.col + k));
+                    if ((found & need) == need) break;
+                }
+        }
+        for (unsigned hm = __ballot_sync(FULL_MASK, need != 0ull && heavy); hm != 0u; hm &= hm - 1u) {
+            const int src = __ffs(hm) - 1;
+            const uint64_t hf = warp_scan_row(F, P.col, __shfl_sync(FULL_MASK, k, src),
+                                              __shfl_sync(FULL_MASK, e, src),
+                                              __shfl_sync(FULL_MASK, need, src));
+            if ((int)lane == src) found = hf;
+        }
+        const uint64_t nx = found & need;
+        if (nx != 0ull) vn[2 * v + 1] = nx;
+    }
+}
+
 // Position of the set bit of rank n (0-based) in x, which has more than n
 // set bits: the largest p with fewer than n + 1 set bits below p.
 __device__ __forceinline__ int nth_set_bit(uint32_t x, int n) {
@@ -1181,11 +1265,10 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
     }
     __syncthreads();
     bool bottom_up = false;
-    if constexpr (!kBatch) {
-        if (dir == 2) {
-            bottom_up_level(P, S, level, nxt, nslot);
-            bottom_up = true;
-        }
+    if (dir == 2) {
+        if constexpr (kBatch) bottom_up_batch_level(P, level);
+        else bottom_up_level(P, S, level, nxt, nslot);
+        bottom_up = true;
     }
     if (!bottom_up) expand_top_down<kBatch, kStaged>(P, S, L, level, dir == 1);
     stage_flush<kBatch>(P, S, level, nxt, nslot);
@@ -1273,6 +1356,24 @@ __device__ void book_level(const TraversalParams& P, const LevelShape& S, int le
     P.stats->edges += S.edges[0] + S.edges[1] + S.edges[2];
 }
 
+// Direction of a batched level: bottom-up when the frontier's degree sum
+// exceeds the degree sum of the vertices some lane has not reached yet plus
+// 4 entries per vertex (a bottom-up level reads every vertex's lane sets),
+// decided afresh each level.  Unlike the single-source rule (Beamer et al.,
+// alpha 15 / beta 18) a bottom-up vertex stops only once it has every lane
+// it lacks, not at its first frontier neighbour, so bottom-up pays off only
+// on the levels whose frontiers cover most of the graph.
+__device__ __forceinline__ int batch_direction(const TraversalParams& P, const LevelShape& L,
+                                               bool prev_bu) {
+    (void)prev_bu;
+    if (P.dir_mode == 0) return 0;
+    if (P.dir_mode == 2) return 2;
+    const long long mf = L.edges[0] + L.edges[1] + L.edges[2];
+    const long long full = (long long)ld_cg_u64(
+        reinterpret_cast<const unsigned long long*>(&P.stats->full_edges));
+    return mf > P.nnz - full + 4 * P.n ? 2 : 0;
+}
+
 // ------------------------------------------- graph-captured level loop
 // End of one loop-body launch (one CTA, thread 0): carry the direction
 // state to the next level and set the while node's condition -- 0 when the
@@ -1314,6 +1415,7 @@ __device__ void graph_advance_batch(const TraversalParams& P) {
     for (int b = 0; b < kBins; ++b)
         nf_next += (long long)(ld_cg_u64(&P.ctl[nslot].packed[b]) >> kCountShift);
     st->graph_level = level + 1;
+    st->graph_prev_bu = st->graph_dir == 2 ? 1 : 0;
     unsigned go = (nf_next > 0 && ld_volatile_i32(&st->status) == 0) ? 1u : 0u;
     if (go && P.dist_int8 && level + 2 > 126) {
         raise_status(P, kDevDepth);
@@ -1423,9 +1525,15 @@ __device__ void init_batch(const TraversalParams& P, long long tid, long long nt
         P.stats->edges = 0;
         P.stats->status = 0;
         P.stats->max_level = 0;
+        P.stats->bu_levels = 0;
         P.stats->graph_level = 0;
+        P.stats->graph_seen = 0;
+        P.stats->graph_prev_bu = 0;
+        P.stats->graph_dir = 0;
+        P.stats->full_edges = 0;
     }
     fill_u64(P.lane_vn, 2 * P.n, tid, nthreads);
+    if (P.dir_mode != 0) fill_u64(P.lane_front, P.n, tid, nthreads);
     // distances are not filled here: emit_batch writes every (lane, vertex)
 }
 
@@ -1492,12 +1600,16 @@ __device__ void seed_batch(const TraversalParams& P, Stage<true>& S) {
             }
             r = P.old2new ? __ldg(P.old2new + cr) : cr;
             record_lane_level(P, i, r, cr, 0);
-            if (first) P.lane_vn[2 * (long long)r] = mask;
+            if (first) {
+                P.lane_vn[2 * (long long)r] = mask;
+                if (P.dir_mode != 0) P.lane_front[r] = mask;
+            }
         }
         stage_push<true>(P, S, first, r, 0, mask, -1, 0, 0);
     }
     stage_flush<true>(P, S, -1, 0, 0);
     if (lane == 0) {
+        P.ctl[0].front_lanes = P.nlanes >= 64 ? ~0ull : ((1ull << P.nlanes) - 1ull);
         P.stats->reached = P.nlanes;
         P.stats->edges = (long long)S.edges;
         P.stats->levels = 1;
@@ -1523,7 +1635,9 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
                             long long nthreads) {
     const int nslot = (level + 1) % 3, nxt = (level + 1) & 1;
     const unsigned lane = lane_id();
-    long long my_pairs = 0;
+    long long my_pairs = 0, my_full = 0;
+    unsigned long long my_front = 0ull;  // lanes with a vertex in the next frontier
+    const uint64_t all_lanes = P.nlanes >= 64 ? ~0ull : ((1ull << P.nlanes) - 1ull);
     const long long nround = (P.n + 31) / 32 * 32;  // warp-uniform trip count
     for (long long v = tid; v < nround; v += nthreads) {
         uint64_t fresh = 0ull;
@@ -1536,7 +1650,12 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
                 reached_before = vn.x != 0ull;
                 *pv = make_ulonglong2(vn.x | fresh, 0ull);
                 my_pairs += __popcll(fresh);
+                // bottom-up bookkeeping: edges of vertices every lane has now reached
+                if (P.dir_mode != 0 && fresh != 0ull && (vn.x | fresh) == all_lanes)
+                    my_full += __ldg(P.off + v + 1) - __ldg(P.off + v);
             }
+            if (P.dir_mode != 0) P.lane_front[v] = fresh;
+            my_front |= fresh;
         }
         // levels: one read-modify-write of the vertex's 64-byte level row
         // (16-byte accesses, consecutive vertices' rows adjacent), bytes of
@@ -1572,6 +1691,16 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
                          nslot);
     }
     stage_flush<true>(P, S, level, nxt, nslot);
+    if (P.dir_mode != 0) {
+        my_full = warp_incl_scan(my_full);
+        if (lane == 31 && my_full > 0)
+            atomicAdd(reinterpret_cast<unsigned long long*>(&P.stats->full_edges),
+                      (unsigned long long)my_full);
+        const unsigned flo = __reduce_or_sync(FULL_MASK, (unsigned)my_front);
+        const unsigned fhi = __reduce_or_sync(FULL_MASK, (unsigned)(my_front >> 32));
+        const unsigned long long fr = ((unsigned long long)fhi << 32) | flo;
+        if (lane == 0 && fr != 0ull) atomicOr(&P.ctl[nslot].front_lanes, fr);
+    }
     my_pairs = warp_incl_scan(my_pairs);
     if (lane == 31 && my_pairs > 0) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&P.ctl[nslot].new_lanes),
@@ -1607,6 +1736,7 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
         seed_batch(P, S);
         if (grid_barrier(P)) {
             stamp(P, 2);
+            bool prev_bu = false;
             for (int level = 0;; ++level) {
                 const LevelShape L = read_level(P, level);
                 if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) break;
@@ -1615,7 +1745,10 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
                     break;
                 }
                 book_batch_level(P, level);
-                expand_level<true>(P, S, L, level, nullptr);
+                const int dir = batch_direction(P, L, prev_bu);
+                if (dir == 2 && blockIdx.x == 0 && threadIdx.x == 0) P.stats->bu_levels += 1;
+                expand_level<true>(P, S, L, level, nullptr, dir);
+                prev_bu = dir == 2;
                 if (!grid_barrier(P)) break;
                 stamp(P, 3 + 2 * level);
                 sweep_batch(P, S, level, tid, nthreads);
@@ -1662,7 +1795,12 @@ bfs_batch_step(const __grid_constant__ TraversalParams P) {
         const LevelShape L = read_level(P, level);
         if (L.cnt[0] + L.cnt[1] + L.cnt[2] == 0) return;
         book_batch_level(P, level);
-        expand_level<true>(P, S, L, level, nullptr);
+        const int dir = batch_direction(P, L, ld_volatile_i32(&P.stats->graph_prev_bu) != 0);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            P.stats->graph_dir = dir;
+            if (dir == 2) P.stats->bu_levels += 1;
+        }
+        expand_level<true>(P, S, L, level, nullptr, dir);
     } else if (P.phase == 8) {
         sweep_batch(P, S, ld_volatile_i32(&P.stats->graph_level), tid, nthreads);
     } else if (P.phase == 9) {

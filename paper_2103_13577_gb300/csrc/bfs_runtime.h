@@ -48,6 +48,7 @@ struct Workspace {
     DevStats* stats = nullptr;
     uint32_t* fb[3] = {nullptr, nullptr, nullptr};  // plain: frontier bitmaps
     uint64_t* lane_vn = nullptr;       // batched: [n][2] visited / next lane sets
+    uint64_t* lane_front = nullptr;    // batched: [n] frontier lane sets (bottom-up levels)
     uint8_t* lane_level = nullptr;     // batched: [n][64] level bytes
     int32_t* roots = nullptr;          // [64]
     int32_t* dist_scratch = nullptr;   // host-output staging (plain: n; batched: none)

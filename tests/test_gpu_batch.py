@@ -153,3 +153,39 @@ def test_batch_bad_arguments(ctx):
         g.run_batch(np.array([3, 10], dtype=np.int32), d[:2])
     assert e.value.status == bfs.BFS_ERR_ROOT_RANGE
     g.close()
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("k", [1, 17, 64])
+def test_batch_direction_optimizing(ctx, kron14, mode, k):
+    """Batched bottom-up levels (frontier lane sets of the neighbours ORed
+    until every missing lane is found) give the oracle's rows."""
+    off, col = kron14
+    roots = graphgen.pick_roots(off, k, seed=300 + k)
+    g = bfs.Graph(ctx, off, col)
+    g.set_option(bfs.BFS_OPT_DIRECTION, mode)
+    ref, _ = expected(off, col, roots)
+    for flags in (0, bfs.BFS_GRAPH_LOOP):
+        d, st = batch_gpu(g, len(off) - 1, roots, flags=flags)
+        assert np.array_equal(d, ref)
+        if mode == 2:
+            assert st["bottom_up_levels"] > 0
+    d8, _ = batch_gpu(g, len(off) - 1, roots, dtype=torch.int8, flags=bfs.BFS_DIST_INT8)
+    assert np.array_equal(d8.astype(np.int32), ref)
+    g.set_option(bfs.BFS_OPT_DIRECTION, 0)
+    d0, st0 = batch_gpu(g, len(off) - 1, roots)
+    assert np.array_equal(d0, ref) and st0["bottom_up_levels"] == 0
+    g.close()
+
+
+def test_batch_bottom_up_other_graphs(ctx):
+    for name, (off, col) in (("grid", G.grid(30, 40)), ("union", G.disjoint_union(G.path(40), G.star(200))),
+                             ("er", G.random_graph(3000, 12000, seed=9))):
+        n = len(off) - 1
+        roots = np.array([0, 1, n // 2, n - 1, 0], dtype=np.int32)
+        g = bfs.Graph(ctx, off, col)
+        g.set_option(bfs.BFS_OPT_DIRECTION, 2)
+        d, _ = batch_gpu(g, n, roots)
+        ref, _ = expected(off, col, roots)
+        assert np.array_equal(d, ref), name
+        g.close()
