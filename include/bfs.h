@@ -257,9 +257,10 @@ bfs_status bfs_batch_sync(bfs_graph* g, void* stream, bfs_run_stats* stats);
  * A server keeps graphs resident and runs single-root queries as they
  * arrive.  Queries on the same graph that are waiting together are packed
  * into one batched launch of up to 64 lanes; when only a few wait, they run
- * as that many single-source traversals instead (bfs_server_add_graph times
- * one of each on the graph to place the cut-over, using the graph's own
- * options, e.g. BFS_OPT_DIRECTION).  Launches run on num_streams CUDA
+ * as that many single-source traversals instead -- while their mean
+ * completion time, t_single (k + 1) / 2, is no later than one batched
+ * launch's (bfs_server_add_graph times one of each on the graph, using the
+ * graph's own options, e.g. BFS_OPT_DIRECTION).  Launches run on num_streams CUDA
  * streams so work from different graphs overlaps on the device.  A launch is
  * admitted only while the device memory of all launches in flight stays
  * within memory_budget bytes; queries that do not fit wait.  A query whose

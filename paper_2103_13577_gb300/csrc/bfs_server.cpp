@@ -55,8 +55,9 @@ struct Launch {
 };
 
 // Per-graph launch policy: up to plain_max waiting queries are served as
-// that many single-source traversals (cheaper than one batched launch,
-// whose cost barely depends on how many lanes it carries); more go batched.
+// that many single-source traversals (their mean completion time is no
+// later than one batched launch's, whose cost barely depends on how many
+// lanes it carries); more go batched.
 struct GraphPolicy {
     int32_t plain_max = 0;
     double plain_ms = 0.0, batch_ms = 0.0;
@@ -363,7 +364,10 @@ bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id) 
         if (st != BFS_OK) return st;
         pol.plain_ms = tp;
         pol.batch_ms = tb;
-        pol.plain_max = tp > 0.f ? std::min(63, std::max(0, (int)(tb / tp))) : 0;
+        // k waiting queries run one by one complete on average after
+        // tp (k + 1) / 2, batched after tb: single-source runs while that is
+        // no later (the batched launch wins once queues are long)
+        pol.plain_max = tp > 0.f ? std::min(63, std::max(0, (int)(2.f * tb / tp) - 1)) : 0;
     }
     std::lock_guard<std::mutex> lk(s->mu);
     s->graphs.push_back(g);
