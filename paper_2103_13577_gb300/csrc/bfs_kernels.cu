@@ -11,20 +11,27 @@
 // GB300 design:
 //  * The whole level loop runs inside one cooperative persistent launch
 //    (grid = resident CTAs of all 152 SMs) separated by a grid barrier
-//    whose wait is bounded by %globaltimer, so no per-level host round trip.
+//    whose wait is bounded by %globaltimer, so no per-level host round trip;
+//    the same level kernels also run as the body of a CUDA-graph while loop
+//    (phases 5-9 of the step kernels) or one launch per level from the host.
 //  * Load balancing replaces the paper's Logarithmic Radix Binning (one
 //    kernel per log2-degree bin, Section "Load Balanced Traversals Per
 //    compute-node") with three degree bins written while the next frontier
-//    is built: deg < t_small (one lane per vertex, edges spread over the warp
-//    by a scan), t_small <= deg < t_large (one warp per vertex, 128-bit
-//    column loads) and deg >= t_large (one CTA per chunk of chunk_cta edges;
+//    is built: deg < t_small (edges of 32 vertices spread over the warp by a
+//    scan), t_small <= deg < t_large (warp chunks of 16-byte column units
+//    over several rows, 128-bit loads) and deg >= t_large (CTA chunks;
 //    heavy vertices span many CTAs).  Each bin counter packs (entries << 34 |
-//    edge prefix) so that one 64-bit atomicAdd per warp reserves queue slots
+//    edge prefix) so that one 64-bit atomicAdd per bin reserves queue slots
 //    and edge ranges at once; warp and CTA work items are fixed-size edge
 //    chunks, located through a chunk-start table filled at enqueue time.
+//  * Probes read the visited bitmap with plain loads, 8 per lane in flight;
+//    the atomicOr claims are batched -- per probe round when it has many
+//    candidates, otherwise per 64-entry stage at flush time.
 //  * The batched traversal carries a 64-bit source-lane set per vertex:
-//    phase A ORs the frontier lanes into next[u], phase B (a sweep) turns the
-//    lanes that are new into distances and the next frontier.
+//    phase A ORs the frontier lanes into next[u] (or, bottom-up, ORs the
+//    neighbours' frontier lanes into each vertex that lacks some), phase B
+//    (a sweep) turns the lanes that are new into distances and the next
+//    frontier.
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -198,13 +205,14 @@ __device__ void kernel_exit(const TraversalParams& P) {
 }
 
 // --------------------------------------------------------------- enqueue
-// Claimed vertices are staged per warp in shared memory and appended to the
-// next frontier up to 64 at a time (measured faster than 256 on GB300).
-// The flush does the per-vertex work that needs random reads (degree from
-// the row offsets, caller numbering) for the whole group at once, writes the
-// distances and parents, bins the group by degree, and reserves queue slots
-// and edge ranges with one 64-bit
-// atomicAdd per bin (the bin counter packs entries << 34 | edge prefix).
+// Candidate vertices (claimed or still to claim) are staged per warp in
+// shared memory and appended to the next frontier up to 64 at a time
+// (measured faster than 32, 128 and 256 on GB300).  The flush claims the
+// unclaimed ones, does the per-vertex work that needs random reads (degree
+// from the row offsets, caller numbering) for the whole group at once,
+// writes the distances and parents, bins the group by degree, and reserves
+// queue slots and edge ranges with one 64-bit atomicAdd per bin (the bin
+// counter packs entries << 34 | edge prefix).
 #ifndef BFS_STAGE_CAP
 #define BFS_STAGE_CAP 64
 #endif
