@@ -563,9 +563,8 @@ def serve_arm(args):
     clock minus the scheduled arrival; the result copy to the caller's pinned
     host buffer is inside it.  Baseline: the same arrivals served one at a
     time by bfs_run (FIFO, arrival order), from measured per-graph service
-    times."""
-    import queue as queue_mod
-
+    times.  The trace is replayed by bfs_server_replay (native submitter and
+    collector threads)."""
     import torch
 
     import graphgen
@@ -585,9 +584,7 @@ def serve_arm(args):
     for gr in graphs:
         gr["gid"] = srv.add_graph(gr["g"])
         nbuf = int(max(8, min(256, (2 << 30) // (gr["n"] * 4))))
-        gr["pool"] = queue_mod.Queue()
-        for _ in range(nbuf):
-            gr["pool"].put(torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy())
+        gr["bufs"] = torch.empty((nbuf, gr["n"]), dtype=torch.int32, pin_memory=True).numpy()
 
     # baseline service times: bfs_run with a pinned host output, per graph
     svc = []
@@ -611,38 +608,14 @@ def serve_arm(args):
         ridx = rng.integers(0, 256, nq)
         t0 = time.monotonic_ns() + 20_000_000
         arrival = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
-        tickets = [None] * nq
-        bufs = [None] * nq
-        done = np.zeros(nq, dtype=np.int64)
-        submitted = queue_mod.Queue()
-        errors = []
-
-        def collector():
-            for _ in range(nq):
-                i = submitted.get()
-                gr = graphs[which[i]]
-                st = srv.wait(tickets[i], 60_000_000)
-                stat, _, _, dn = srv.times(tickets[i])
-                if stat != bfs.BFS_OK:
-                    errors.append(stat)
-                done[i] = dn
-                srv.release(tickets[i])
-                gr["pool"].put(bufs[i])
-
-        th = threading.Thread(target=collector)
-        th.start()
-        for i in range(nq):
-            gr = graphs[which[i]]
-            while True:
-                now = time.monotonic_ns()
-                if now >= arrival[i]:
-                    break
-                if arrival[i] - now > 300_000:
-                    time.sleep((arrival[i] - now - 200_000) / 1e9)
-            bufs[i] = gr["pool"].get()
-            tickets[i] = srv.submit(gr["gid"], int(gr["roots"][ridx[i]]), bufs[i])
-            submitted.put(i)
-        th.join()
+        # the trace is submitted and collected by the library's native replay
+        # threads (no Python in the loop); a query takes any free pinned buffer
+        # of its graph and waits for one when all are in use
+        gid = np.array([graphs[w]["gid"] for w in which], dtype=np.int32)
+        rts = np.array([graphs[w]["roots"][j] for w, j in zip(which, ridx)], dtype=np.int32)
+        done, status, _ = srv.replay(gid, rts, arrival, [gr["bufs"] for gr in graphs],
+                                     timeout_us=60_000_000)
+        errors = [int(x) for x in status if x != bfs.BFS_OK]
         lat_ms = (done - arrival) / 1e6
         span_s = (done.max() - arrival[0]) / 1e9
         # FIFO model of the same arrivals served one query at a time

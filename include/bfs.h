@@ -292,6 +292,24 @@ typedef struct bfs_server_stats {
     int64_t max_inflight_bytes;
 } bfs_server_stats;
 bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out);
+
+/* Replays a query trace against the server from native threads (load
+ * generation with nothing of the caller's runtime in the loop).  Query i is
+ * submitted at arrival_ns[i] (steady clock, the clock of bfs_ticket_times;
+ * non-decreasing) on graph graph_ids[i] with root roots[i].  Its row goes to
+ * one of bufs_per_graph[g] host buffers of graph g: graph_bufs[g] points to
+ * bufs_per_graph[g] consecutive rows of n_g int32 (pinned memory keeps the
+ * copies fast); a query takes any free buffer of its graph and waits for
+ * one to come back if none is free (a buffer returns when its query
+ * completes).  On return (every query done) done_ns[i] is the query's
+ * completion time on the server's clock, status_out[i] its status and, when
+ * slot_out is not NULL, slot_out[i] the buffer it used.  Waits inside are
+ * bounded by timeout_us per query (negative: none). */
+bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids,
+                             const int32_t* roots, const int64_t* arrival_ns,
+                             int32_t* const* graph_bufs, const int32_t* bufs_per_graph,
+                             int64_t timeout_us, int64_t* done_ns, int32_t* status_out,
+                             int32_t* slot_out);
 /* Stops the server; queued queries finish with BFS_ERR_CANCELLED. */
 bfs_status bfs_server_destroy(bfs_server* s);
 

@@ -72,6 +72,7 @@ from .api import (  # noqa: F401
     bfs_server_create,
     bfs_server_destroy,
     bfs_server_get_stats,
+    bfs_server_replay,
     bfs_submit,
     bfs_ticket_times,
     bfs_wait,

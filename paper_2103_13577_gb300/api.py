@@ -269,6 +269,35 @@ def bfs_server_get_stats(s: int) -> dict:
     return {f: getattr(st, f) for f, _ in ServerStats._fields_}
 
 
+def bfs_server_replay(s: int, graph_ids, roots, arrival_ns, graph_bufs, timeout_us: int = -1):
+    """Replay a query trace from native threads (see include/bfs.h).
+    graph_bufs: one C-contiguous int32 host array [k_g, n_g] per graph (pinned
+    memory keeps the copies fast).  Returns (done_ns, status, slot) arrays."""
+    gid = np.ascontiguousarray(graph_ids, dtype=np.int32)
+    rts = np.ascontiguousarray(roots, dtype=np.int32)
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    nq = len(gid)
+    if len(rts) != nq or len(arr) != nq:
+        raise ValueError("graph_ids, roots and arrival_ns must have the same length")
+    ptrs = (ctypes.c_void_p * len(graph_bufs))()
+    counts = np.zeros(len(graph_bufs), dtype=np.int32)
+    for i, b in enumerate(graph_bufs):
+        p, dev = _buf(b, np.int32)
+        if dev:
+            raise ValueError("replay buffers are host memory")
+        ptrs[i] = p
+        counts[i] = b.shape[0]
+    done = np.zeros(nq, dtype=np.int64)
+    status = np.zeros(nq, dtype=np.int32)
+    slot = np.zeros(nq, dtype=np.int32)
+    check(_lib.lib().bfs_server_replay(s, nq, gid.ctypes.data, rts.ctypes.data, arr.ctypes.data,
+                                       ctypes.cast(ptrs, ctypes.c_void_p), counts.ctypes.data,
+                                       int(timeout_us), done.ctypes.data, status.ctypes.data,
+                                       slot.ctypes.data),
+          "bfs_server_replay")
+    return done, status, slot
+
+
 def bfs_server_destroy(s: int) -> None:
     check(_lib.lib().bfs_server_destroy(s), "bfs_server_destroy")
 
@@ -364,6 +393,9 @@ class Server:
 
     def stats(self) -> dict:
         return bfs_server_get_stats(self.handle)
+
+    def replay(self, graph_ids, roots, arrival_ns, graph_bufs, timeout_us: int = -1):
+        return bfs_server_replay(self.handle, graph_ids, roots, arrival_ns, graph_bufs, timeout_us)
 
     def close(self):
         if self.handle:

@@ -485,6 +485,144 @@ bfs_status bfs_release(bfs_server* s, bfs_ticket ticket) {
     return BFS_OK;
 }
 
+bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids,
+                             const int32_t* roots, const int64_t* arrival_ns,
+                             int32_t* const* graph_bufs, const int32_t* bufs_per_graph,
+                             int64_t timeout_us, int64_t* done_ns, int32_t* status_out,
+                             int32_t* slot_out) {
+    if (!s || nq < 0 || (nq > 0 && (!graph_ids || !roots || !arrival_ns || !graph_bufs ||
+                                    !bufs_per_graph || !done_ns || !status_out))) {
+        set_error("null argument");
+        return BFS_ERR_INVALID_ARG;
+    }
+    std::vector<int64_t> ns;  // vertices per graph
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        for (auto* g : s->graphs) ns.push_back(g->n);
+    }
+    const int ng = (int)ns.size();
+    for (int64_t i = 0; i < nq; ++i)
+        if (graph_ids[i] < 0 || graph_ids[i] >= ng || bufs_per_graph[graph_ids[i]] < 1 ||
+            !graph_bufs[graph_ids[i]]) {
+            set_error("replay: unknown graph or no buffers for it");
+            return BFS_ERR_INVALID_ARG;
+        }
+    // per-graph free buffers
+    std::vector<std::vector<int>> free_slots(ng);
+    for (int g = 0; g < ng; ++g)
+        for (int k = std::max(0, bufs_per_graph[g]) - 1; k >= 0; --k) free_slots[g].push_back(k);
+    std::vector<bfs_ticket> tickets((size_t)nq, 0);
+    std::vector<int> slot_of((size_t)nq, 0);
+    std::mutex mu;
+    std::condition_variable cv;
+    int64_t submitted = 0;
+    bfs_status first_err = BFS_OK;
+    for (int64_t i = 0; i < nq; ++i) {
+        done_ns[i] = 0;
+        status_out[i] = BFS_PENDING;
+    }
+    // collector: takes each query's result as soon as it completes (in any
+    // order, so a long query does not hold the buffers of later ones)
+    std::thread collector([&] {
+        std::vector<int64_t> open, fin;
+        std::vector<int64_t> opened_at;
+        int64_t taken = 0;
+        for (;;) {
+            {
+                std::lock_guard<std::mutex> lk(mu);
+                while (taken < submitted) {
+                    open.push_back(taken++);
+                    opened_at.push_back(now_ns());
+                }
+                if (open.empty() && (taken == nq || first_err != BFS_OK)) break;
+            }
+            fin.clear();
+            {
+                std::unique_lock<std::mutex> lk(s->mu);
+                auto any_done = [&] {
+                    for (int64_t j : open) {
+                        auto it = s->tickets.find(tickets[(size_t)j]);
+                        if (it == s->tickets.end() || it->second->status != BFS_PENDING) return true;
+                    }
+                    return false;
+                };
+                s->cv_done.wait_for(lk, std::chrono::microseconds(200), any_done);
+                for (size_t a = 0; a < open.size();) {
+                    const int64_t j = open[a];
+                    auto it = s->tickets.find(tickets[(size_t)j]);
+                    const bool done = it == s->tickets.end() || it->second->status != BFS_PENDING;
+                    const bool expired =
+                        !done && timeout_us >= 0 && now_ns() - opened_at[a] > timeout_us * 1000;
+                    if (!done && !expired) {
+                        ++a;
+                        continue;
+                    }
+                    if (it != s->tickets.end()) {
+                        done_ns[j] = it->second->done_ns;
+                        status_out[j] = expired ? BFS_ERR_TIMEOUT : it->second->status;
+                        if (!expired) s->tickets.erase(it);
+                    } else {
+                        status_out[j] = BFS_ERR_NOT_FOUND;
+                    }
+                    fin.push_back(j);
+                    open[a] = open.back();
+                    open.pop_back();
+                    opened_at[a] = opened_at.back();
+                    opened_at.pop_back();
+                }
+            }
+            if (!fin.empty()) {
+                std::lock_guard<std::mutex> lk(mu);
+                for (int64_t j : fin) {
+                    if (slot_out) slot_out[j] = slot_of[(size_t)j];
+                    if (status_out[j] == BFS_ERR_TIMEOUT) first_err = BFS_ERR_TIMEOUT;
+                    else free_slots[graph_ids[j]].push_back(slot_of[(size_t)j]);
+                }
+                cv.notify_all();
+            }
+        }
+    });
+    for (int64_t i = 0; i < nq; ++i) {
+        const int g = graph_ids[i];
+        int slot = 0;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            auto any_free = [&] { return !free_slots[g].empty(); };
+            if (timeout_us < 0) cv.wait(lk, any_free);
+            else if (!cv.wait_for(lk, std::chrono::microseconds(timeout_us), any_free)) {
+                first_err = BFS_ERR_TIMEOUT;
+                cv.notify_all();
+                break;
+            }
+            slot = free_slots[g].back();
+            free_slots[g].pop_back();
+        }
+        for (;;) {  // until the arrival time
+            const int64_t now = now_ns();
+            if (now >= arrival_ns[i]) break;
+            if (arrival_ns[i] - now > 200000)
+                std::this_thread::sleep_for(std::chrono::nanoseconds(arrival_ns[i] - now - 100000));
+        }
+        bfs_ticket t = 0;
+        const bfs_status st =
+            bfs_submit(s, g, roots[i], graph_bufs[g] + (size_t)slot * (size_t)ns[(size_t)g], &t);
+        std::lock_guard<std::mutex> lk(mu);
+        if (st != BFS_OK) {
+            first_err = st;
+            free_slots[g].push_back(slot);
+            cv.notify_all();
+            break;
+        }
+        tickets[(size_t)i] = t;
+        slot_of[(size_t)i] = slot;
+        ++submitted;
+        cv.notify_all();
+    }
+    collector.join();
+    if (first_err != BFS_OK) return first_err;
+    return BFS_OK;
+}
+
 bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out) {
     if (!s || !out) {
         set_error("null argument");

@@ -89,3 +89,36 @@ def test_budget_rejection_and_poll(setup):
         srv.poll(12345)
     assert e.value.status == bfs.BFS_ERR_NOT_FOUND
     srv.close()
+
+
+def test_native_replay(setup):
+    """bfs_server_replay submits a timed trace from native threads, reusing a
+    few output buffers per graph; every query completes after its arrival and
+    each buffer ends up holding its last query's row."""
+    ctx, graphs = setup
+    srv = bfs.Server(ctx, 512 << 20, num_streams=3)
+    gids = [srv.add_graph(g) for _, _, g in graphs]
+    rng = np.random.default_rng(7)
+    nq = 120
+    which = rng.integers(0, len(graphs), nq).astype(np.int32)
+    roots = np.array([int(graphgen.pick_roots(graphs[w][0], 1, seed=2000 + i)[0])
+                      for i, w in enumerate(which)], dtype=np.int32)
+    arrival = time.monotonic_ns() + 5_000_000 + np.cumsum(rng.exponential(100_000, nq)).astype(np.int64)
+    k = 3
+    bufs = [np.full((k, len(off) - 1), -7, dtype=np.int32) for off, _, _ in graphs]
+    done, status, slot = srv.replay(np.array(gids, dtype=np.int32)[which], roots, arrival, bufs,
+                                    timeout_us=30_000_000)
+    assert np.all(status == bfs.BFS_OK)
+    assert np.all(done >= arrival)
+    assert np.all((slot >= 0) & (slot < k))
+    # each buffer holds the row of the last-completed query that used it
+    for gi, (off, col, _) in enumerate(graphs):
+        for sl in range(k):
+            mine = np.nonzero((which == gi) & (slot == sl))[0]
+            if len(mine) == 0:
+                continue
+            last = mine[np.argmax(done[mine])]
+            ref, _, _ = oracle.bfs(off, col, int(roots[last]))
+            assert np.array_equal(bufs[gi][sl], ref)
+    assert srv.stats()["completed"] == nq
+    srv.close()
