@@ -1,0 +1,80 @@
+"""Host-side logic checked without a GPU: the level-direction rule the
+device and host loops share (compiled from the library's own header with
+the host compiler), and the ncu launch-list summariser behind profiles/."""
+from __future__ import annotations
+
+import os
+import subprocess
+import textwrap
+
+import pytest
+
+from paper_2103_13577_gb300 import profiling
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_2103_13577_gb300", "csrc")
+
+DIRECTION_PROBE = textwrap.dedent(r"""
+    #define __host__
+    #define __device__
+    #include <cstdio>
+    #include "bfs_internal.h"
+    using bfs::choose_direction;
+    int main() {
+        const long long n = 1000000;
+        // mode 0: top-down, bitmap order above n / bitmap_div frontier vertices
+        printf("%d %d %d\n", choose_direction(0, false, 900, 10, 10, n, 15, 18, 0),
+               choose_direction(0, false, 10, 10, 200000, n, 15, 18, 8),
+               choose_direction(0, false, 10, 10, 100000, n, 15, 18, 8));
+        // mode 2: bottom-up on every level
+        printf("%d\n", choose_direction(2, false, 1, 1000000, 1, n, 15, 18, 0));
+        // mode 1 from top-down: bottom-up once m_f * alpha > m_u
+        printf("%d %d\n", choose_direction(1, false, 100, 1499, 5, n, 15, 18, 0),
+               choose_direction(1, false, 100, 1500, 5, n, 15, 18, 0));
+        // mode 1 from bottom-up: back to top-down once n_f * beta < n
+        printf("%d %d\n", choose_direction(1, true, 1, 1, 55555, n, 15, 18, 0),
+               choose_direction(1, true, 1, 1, 55556, n, 15, 18, 0));
+        return 0;
+    }
+""")
+
+
+def test_direction_rule(tmp_path):
+    src = tmp_path / "probe.cpp"
+    exe = tmp_path / "probe"
+    src.write_text(DIRECTION_PROBE)
+    try:
+        subprocess.check_call(["g++", "-std=c++17", "-I", CSRC, str(src), "-o", str(exe)])
+    except (OSError, subprocess.CalledProcessError):
+        pytest.skip("no host C++ compiler")
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    assert out[0].split() == ["0", "1", "0"]   # 200000 * 8 > n; 100000 * 8 < n
+    assert out[1].split() == ["2"]
+    assert out[2].split() == ["2", "0"]        # 100 * 15 > 1499, not > 1500
+    assert out[3].split() == ["0", "2"]        # 55555 * 18 < 1e6 <= 55556 * 18
+
+
+def test_launch_list_summary(tmp_path):
+    csv_path = tmp_path / "l.csv"
+    rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
+    for i in range(3):
+        rows.append(f'"{2 * i}","void bfs::bfs_plain_persistent<4, 0>(bfs::TraversalParams)",'
+                    f'"gpu__time_duration.sum","usecond","{500 + i}"')
+        rows.append(f'"{2 * i}","void bfs::bfs_plain_persistent<4, 0>(bfs::TraversalParams)",'
+                    f'"dram__bytes_read.sum","Mbyte","{700 + i}"')
+        rows.append(f'"{2 * i}","void bfs::bfs_plain_persistent<4, 0>(bfs::TraversalParams)",'
+                    f'"dram__bytes_write.sum","Mbyte","100"')
+        rows.append(f'"{2 * i + 1}","void bfs::rel_columns_kernel(int)","gpu__time_duration.sum",'
+                    f'"usecond","50"')
+    csv_path.write_text("==PROF== noise\n" + "\n".join(rows) + "\n")
+    md = tmp_path / "out.md"
+    js = tmp_path / "out.json"
+    profiling.summarize(str(csv_path), str(md), "bfs_plain_persistent", str(js), "cmd")
+    text = md.read_text()
+    assert "bfs::bfs_plain_persistent<4, 0>" in text or "bfs_plain_persistent<4, 0>" in text
+    assert "| 3 |" in text
+    import json
+    t = json.loads(js.read_text())
+    assert t["launches"] == 3
+    assert abs(t["dram_bytes_per_launch"] - 801e6) < 1e3
+    assert t["kernel_sha256_16"] == profiling.kernel_hash()
