@@ -45,6 +45,7 @@ METRIC = "BFS GTEPS (hmean over 64 roots) plain vs 64-root batched; query p50/p9
 WORKLOAD = "kronecker_s22_ef16_plain_64roots"
 KERNEL_SRC = os.path.join(ROOT, "paper_2103_13577_gb300", "csrc", "bfs_kernels.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_plain_persistent_kron_s22_traffic.json")
+BATCH_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_batch_persistent_kron_s22_traffic.json")
 
 
 def env_int(name, default):
@@ -79,11 +80,11 @@ def kernel_hash():
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(path=TRAFFIC_FILE):
     """DRAM bytes per launch from the committed ncu capture, or None when the
     kernel source changed since the capture."""
     try:
-        with open(TRAFFIC_FILE) as f:
+        with open(path) as f:
             rec = json.load(f)
         if rec.get("kernel_sha256_16") != kernel_hash():
             return None
@@ -380,6 +381,12 @@ def gpu_arm(args, rank, world, local_rank):
     bst = g.batch_sync(stream)
     batch_ms = bev[0].elapsed_time(bev[1]) / reps
     batch_gteps = bst["edges_scanned"] / (batch_ms * 1e-3) / 1e9
+    # algorithmic bytes of the batched launch from its frontiers (the rows)
+    from paper_2103_13577_gb300 import profiling
+    deg_dev = torch.from_numpy(np.diff(off)).to(dev_)
+    b_sizes, b_degs, b_reached = profiling.batch_frontier_sums(bd, deg_dev)
+    b_bytes = profiling.batch_algorithmic_bytes(b_sizes, b_degs, b_reached, n, NROOTS, 4)
+    del deg_dev
     g.set_option(bfs.BFS_OPT_DIRECTION, 1)
     g.run_batch(roots, bd, stream=stream)
     g.batch_sync(stream)
@@ -393,6 +400,7 @@ def gpu_arm(args, rank, world, local_rank):
 
     # roofline of the traversal kernel (one launch per root)
     peak, peak_kind = measured_hbm_peak()
+    b_achieved = b_bytes / (batch_ms * 1e-3) / 1e9
     alg_bytes = 4.0 * m_c + 32.0 * n_c + 8.125 * n
     achieved = float(np.mean(alg_bytes / (t_root * 1e-3)) / 1e9)
     traffic = recorded_traffic()
@@ -453,6 +461,13 @@ def gpu_arm(args, rank, world, local_rank):
             "batched": {"roots": NROOTS, "ms": batch_ms, "gteps": batch_gteps,
                         "edges": int(bst["edges_scanned"]), "levels": int(bst["levels"]),
                         "speedup_vs_plain_step": ms_step / batch_ms,
+                        "roofline": {"bound": "hbm", "achieved": b_achieved, "peak": peak,
+                                     "unit": "GB/s", "frac": b_achieved / peak,
+                                     "traffic": recorded_traffic(BATCH_TRAFFIC_FILE),
+                                     "kernel": "bfs_batch_persistent",
+                                     "algorithmic_bytes_per_launch": b_bytes,
+                                     "frontier_entries": int(sum(b_sizes)),
+                                     "frontier_edges": int(sum(b_degs))},
                         "direction_optimizing": {
                             "ms": batch_do_ms,
                             "gteps": bdo["edges_scanned"] / (batch_do_ms * 1e-3) / 1e9,

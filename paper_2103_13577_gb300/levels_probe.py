@@ -2,12 +2,15 @@
 16) and runs two single-source traversals with BFS_HOST_LOOP, so that each
 BFS level is its own kernel launch (one ncu result per level).
 
-  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent|do|timeline]
+  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent|do|timeline|batch]
 
 do: host-loop launches with the direction-optimizing mode.
 timeline: persistent launches with the level timeline attached; prints the
 median time of init, seed and every level over 8 roots, for the L2 column
 prefetch off and on, top-down and direction-optimizing.
+batch: four 64-root batched launches (int32 rows, top-down, persistent) on
+the roots the benchmark uses; prints the mean device time of the last two,
+the frontier sums and the algorithmic bytes of one launch.
 """
 from __future__ import annotations
 
@@ -30,6 +33,11 @@ def main():
     ctx = bfs.Context(0)
     g = bfs.Graph(ctx, off, col)
     n = len(off) - 1
+    if mode == "batch":
+        batch(bfs, g, off, graphgen.pick_roots(off, 64, seed=3))
+        g.close()
+        ctx.close()
+        return
     dist = torch.empty(n, dtype=torch.int32, device="cuda")
     par = torch.empty(n, dtype=torch.int32, device="cuda")
     if mode == "timeline":
@@ -45,6 +53,35 @@ def main():
         print(g.sync(), flush=True)
     g.close()
     ctx.close()
+
+
+def batch(bfs, g, off, roots):
+    import json
+
+    import numpy as np
+    import torch
+
+    from paper_2103_13577_gb300 import profiling
+
+    n = len(off) - 1
+    rows = torch.empty((len(roots), n), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        g.run_batch(roots, rows, stream=stream)
+    g.batch_sync(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record(stream)
+    for _ in range(2):
+        g.run_batch(roots, rows, stream=stream)
+    ev[1].record(stream)
+    st = g.batch_sync(stream)
+    ms = ev[0].elapsed_time(ev[1]) / 2
+    deg = torch.from_numpy(np.diff(off)).cuda()
+    sizes, degs, reached = profiling.batch_frontier_sums(rows, deg)
+    b = profiling.batch_algorithmic_bytes(sizes, degs, reached, n, len(roots), 4)
+    print(json.dumps({"ms": ms, "levels": int(st["levels"]), "edges_scanned": int(st["edges_scanned"]),
+                      "frontier_entries": sizes, "frontier_edges": degs, "reached": reached,
+                      "algorithmic_bytes": b, "gbs": b / (ms * 1e-3) / 1e9}), flush=True)
 
 
 def timeline(bfs, g, roots, dist, par):

@@ -2,7 +2,8 @@
 short summaries kept under profiles/: per kernel its launches, total device
 time and share, and -- when DRAM byte counters were captured -- the DRAM
 traffic per launch of one kernel, stamped with a hash of the kernel source
-so that a stale number is never reported for a changed kernel.
+so that a stale number is never reported for a changed kernel.  Also the
+algorithmic bytes of a batched launch, the numerator of its roofline.
 
 Usage:
   python -m paper_2103_13577_gb300.profiling LAUNCHES.csv OUT.md \
@@ -83,6 +84,41 @@ def summarize(path: str, out_md: str, traffic_kernel: str | None, traffic_json: 
                 json.dump({"kernel": traffic_kernel, "launches": len(flat),
                            "dram_bytes_per_launch": sum(flat) / len(flat),
                            "kernel_sha256_16": kernel_hash(), "command": command}, f, indent=1)
+
+
+def batch_frontier_sums(rows, deg):
+    """Frontiers of a top-down 64-root batched traversal, recovered from its
+    distance rows: for every level L, |A_L| = the vertices some lane reaches
+    at level L (one queue entry each, carrying its lane set) and D_L = the
+    sum of their degrees (the column entries level L expands); plus R = the
+    vertices any lane reaches.  rows: [k][N] distances (-1 unreached, int32
+    or int8), deg: [N] out-degrees; torch tensors on one device."""
+    sizes, degs = [], []
+    top = int(rows.max().item())
+    for level in range(top + 1):
+        a = (rows == level).any(0)
+        sizes.append(int(a.sum().item()))
+        degs.append(int(deg[a].sum().item()))
+    reached = int((rows >= 0).any(0).sum().item())
+    return sizes, degs, reached
+
+
+def batch_algorithmic_bytes(sizes, degs, reached: int, n: int, k: int, elem: int) -> float:
+    """Bytes one top-down batched launch (bfs_batch_persistent) has to move,
+    each item once:
+      init      16 N                 visited/next lane-set pairs cleared
+      level L   4 D_L                column entries of the frontier's rows
+                + 28 |A_L|           two row offsets, queue entry (vertex + lane set)
+                + 16 N               sweep reads every vertex's lane-set pair
+                + 92 |A_L|           producing A_L: pair write-back, 64-byte
+                                     level row, queue entry
+      emit      12 N + 64 R          visited set and renumbering of every vertex,
+                                     level rows of the reached ones
+                + k N elem           the k distance rows
+    Lane-set updates of the neighbours (atomicOr on next) and the level-row
+    re-reads of vertices reached before are cache traffic, not counted."""
+    per_level = sum(4 * d + 120 * a + 16 * n for a, d in zip(sizes, degs))
+    return float(per_level + 16 * n + 12 * n + 64 * reached + k * n * elem)
 
 
 def main():

@@ -78,3 +78,27 @@ def test_launch_list_summary(tmp_path):
     assert t["launches"] == 3
     assert abs(t["dram_bytes_per_launch"] - 801e6) < 1e3
     assert t["kernel_sha256_16"] == profiling.kernel_hash()
+
+
+def test_batch_frontier_sums_path_graph():
+    # path 0-1-2-3-4, lanes rooted at both ends: level 3 holds 3 (lane 0)
+    # and 1 (lane 1), so a vertex enters the frontier once per distinct level
+    import torch
+    rows = torch.tensor([[0, 1, 2, 3, 4], [4, 3, 2, 1, 0], [-1, -1, -1, -1, -1]],
+                        dtype=torch.int8)
+    deg = torch.tensor([1, 2, 2, 2, 1], dtype=torch.int64)
+    sizes, degs, reached = profiling.batch_frontier_sums(rows, deg)
+    assert sizes == [2, 2, 1, 2, 2]
+    assert degs == [2, 4, 2, 4, 2]
+    assert reached == 5
+    b = profiling.batch_algorithmic_bytes(sizes, degs, reached, n=5, k=3, elem=1)
+    # columns 4*14 + per-entry 120*9 + sweeps 16*5*5 + init/emit 28*5 + rows 64*5 + out 3*5
+    assert b == 56 + 1080 + 400 + 140 + 320 + 15
+
+
+def test_batch_frontier_sums_unreached_and_isolated():
+    import torch
+    rows = torch.tensor([[0, -1, 1], [1, -1, 0]], dtype=torch.int32)
+    deg = torch.tensor([1, 0, 1], dtype=torch.int64)
+    sizes, degs, reached = profiling.batch_frontier_sums(rows, deg)
+    assert sizes == [2, 2] and degs == [2, 2] and reached == 2
