@@ -9,13 +9,17 @@ code with it (the only common module is ``graphgen``, which makes inputs).
   Section "Preliminaries": d = infinity), one valid int32 ``parent``, and
   an info dict (levels, per-level vertex counts, scanned entries m_c).
 * ``bfs_multi(off, col, roots)`` -- one independent BFS per root, k x n.
+* ``bfs_paths(off, col, root, weight, lo, hi)`` -- shortest-path counts
+  (Brandes' forward phase) on the entries whose weight lies in [lo, hi]
+  (all entries when ``weight`` is None): int32 ``hops``, float64 ``sigma``.
 * ``check_tree(off, col, root, dist, parent)`` -- Graph500-style checks of a
   BFS result that do not depend on which of several valid parents was
   chosen (used to accept GPU parents).
 
 Pins: ``tests/test_oracle_pins.py`` checks this oracle against Floyd-Warshall
 brute force, closed-form distances, scipy's breadth-first search, and
-union-find components.
+union-find components; ``tests/test_oracle_paths_pins.py`` checks the path
+counts against walk counts from adjacency-matrix powers and closed forms.
 """
 from __future__ import annotations
 
@@ -63,6 +67,10 @@ def _bind(lib):
     lib.oracle_bfs.restype = ctypes.c_int64
     lib.oracle_bfs_multi.argtypes = [ctypes.c_int64, i64p, i32p, i64p, ctypes.c_int64, i32p, i64p]
     lib.oracle_bfs_multi.restype = ctypes.c_int64
+    lib.oracle_bfs_paths.argtypes = [ctypes.c_int64, i64p, i32p, i32p, ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_int64, i32p,
+                                     ctypes.POINTER(ctypes.c_double), i64p]
+    lib.oracle_bfs_paths.restype = ctypes.c_int64
     return lib
 
 
@@ -115,6 +123,36 @@ def bfs_multi(off, col, roots, lib=None):
     if rc < 0:
         raise RuntimeError(f"oracle_bfs_multi failed ({rc})")
     return dist, scanned[:k]
+
+
+def bfs_paths(off, col, root, weight=None, lo=0, hi=0, lib=None):
+    """Shortest-path counts from ``root`` over the entries e with
+    lo <= weight[e] <= hi (every entry when ``weight`` is None):
+    (hops int32[n], sigma float64[n], info)."""
+    lib = lib or load()
+    off, col = _csr(off, col)
+    n = len(off) - 1
+    if not (0 <= root < n):
+        raise ValueError("root out of range")
+    wp = None
+    if weight is not None:
+        weight = np.ascontiguousarray(weight, dtype=np.int32)
+        if len(weight) < off[-1]:
+            raise ValueError("weight shorter than the column array")
+        if weight.size == 0:
+            weight = np.zeros(1, dtype=np.int32)
+        wp = _p(weight, ctypes.c_int32)
+    hops = np.empty(n, dtype=np.int32)
+    sigma = np.empty(n, dtype=np.float64)
+    scanned = np.zeros(1, dtype=np.int64)
+    nl = lib.oracle_bfs_paths(n, _p(off, ctypes.c_int64), _p(col, ctypes.c_int32), wp, int(lo),
+                              int(hi), int(root), _p(hops, ctypes.c_int32),
+                              _p(sigma, ctypes.c_double), _p(scanned, ctypes.c_int64))
+    if nl < 0:
+        raise RuntimeError(f"oracle_bfs_paths failed ({nl})")
+    info = {"levels": int(nl), "edges_scanned": int(scanned[0]),
+            "reached": int(np.count_nonzero(hops >= 0))}
+    return hops, sigma, info
 
 
 def check_tree(off, col, root, dist, parent, undirected=True):
