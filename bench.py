@@ -154,6 +154,52 @@ def make_workload(rank):
 
 
 # ---------------------------------------------------------------- oracle
+def paths_measure(bfs, torch, dev_, stream, off, col, roots, n):
+    """bfs_run_paths (shortest-path counts) on the caller's CSR resident on
+    the device, every entry kept and with a weight filter keeping weights
+    0-3 of uniform 0-7 (about half the entries); device time per root from
+    CUDA events on the stream, scratch carved from an arena context.
+    Algorithmic bytes per traversal: 4 m_c columns (+ 4 m_c weights when
+    filtered) + 56 n_c (row offsets 16, frontier queue 8, degree and scan
+    arrays 32) + 12 N (hops and sigma initialised); the random hops probes,
+    claims and sigma atomics are cache traffic."""
+    peak, _ = measured_hbm_peak()
+    arena = torch.empty(int(32 * n + (64 << 20)), dtype=torch.uint8, device=dev_)
+    pctx = bfs.Context(dev_.index, arena=arena)
+    d_off = torch.from_numpy(np.ascontiguousarray(off, dtype=np.int64)).to(dev_)
+    d_col = torch.from_numpy(np.ascontiguousarray(col, dtype=np.int32)).to(dev_)
+    wts = np.random.default_rng(5).integers(0, 8, len(col)).astype(np.int32)
+    d_w = torch.from_numpy(wts).to(dev_)
+    hops = torch.empty(n, dtype=torch.int32, device=dev_)
+    sigma = torch.empty(n, dtype=torch.float64, device=dev_)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {"roots": len(roots), "note": "hops + shortest-path counts (Brandes forward phase), "
+           "top-down only; GTEPS = entries of the reached rows / time"}
+    for name, w, lo, hi in (("all_entries", None, 0, 0), ("weights_0_3_of_0_7", d_w, 0, 3)):
+        pctx.run_paths(d_off, d_col, int(roots[0]), hops, sigma, w, lo, hi, stream=stream)
+        ms, edges, nbytes = [], [], []
+        for r in roots:
+            ev[0].record(stream)
+            st = pctx.run_paths(d_off, d_col, int(r), hops, sigma, w, lo, hi, stream=stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev_)
+            ms.append(ev[0].elapsed_time(ev[1]))
+            edges.append(st["edges_scanned"])
+            nbytes.append((8 if w is not None else 4) * st["edges_scanned"] + 56 * st["reached"]
+                          + 12 * n)
+        ms, edges, nbytes = np.array(ms), np.array(edges, dtype=np.float64), np.array(nbytes, dtype=np.float64)
+        gbs = float(np.mean(nbytes / (ms * 1e-3)) / 1e9)
+        out[name] = {"gteps": hmean(edges / (ms * 1e-3) / 1e9), "root_ms_median": float(np.median(ms)),
+                     "levels_last_root": int(st["levels"]),
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                  "frac": gbs / peak, "traffic": None,
+                                  "kernel": "paths_expand with paths_degrees and the scan",
+                                  "algorithmic_bytes_per_traversal": float(nbytes.mean())}}
+    pctx.close()
+    del arena, d_off, d_col, d_w, hops, sigma
+    return out
+
+
 def run_oracle_sample(off, col, roots, budget_s):
     """Serial oracle over as many roots as fit in budget_s (at least one)."""
     import oracle
@@ -367,6 +413,9 @@ def gpu_arm(args, rank, world, local_rank):
         lrb_ms[i] = lev[0].elapsed_time(lev[1])
     lrb_value = hmean(m_c / (lrb_ms * 1e-3) / 1e9)
 
+    # shortest-path counts and weight-filtered traversal (bfs_run_paths)
+    paths = paths_measure(bfs, torch, dev_, stream, off, col, roots[:8], n)
+
     # 64-root batched launch on the same graph (one persistent launch)
     bd = torch.empty((NROOTS, n), dtype=torch.int32, device=dev_)
     for _ in range(2):
@@ -458,6 +507,7 @@ def gpu_arm(args, rank, world, local_rank):
                 "value": lrb_value, "unit": "GTEPS", "root_ms_median": float(np.median(lrb_ms)),
                 "note": "per-level log2-degree binning, one kernel per bin on its own stream, "
                         "host-driven level loop (bfs_run_lrb), same roots, this rank"},
+            "shortest_path_counts": paths,
             "batched": {"roots": NROOTS, "ms": batch_ms, "gteps": batch_gteps,
                         "edges": int(bst["edges_scanned"]), "levels": int(bst["levels"]),
                         "speedup_vs_plain_step": ms_step / batch_ms,

@@ -363,6 +363,45 @@ typedef struct bfs_lrb_stats {
 bfs_status bfs_run_lrb(bfs_graph* g, int32_t root, int32_t* dist, void* stream,
                        bfs_lrb_stats* stats);
 
+/* ---- shortest-path counts and weight-filtered traversal -------------------------
+ * Section "Top Down Vs. Bottom Up" names two uses of BFS that need every
+ * entry leaving the frontier examined (so no bottom-up level): counting all
+ * shortest paths, as betweenness centrality does, and weight-filtering BFS,
+ * which follows only edges of given weights.  This call does both, top-down:
+ * on the subgraph of the CSR entries e with w_lo <= weight[e] <= w_hi (every
+ * entry when weight is NULL; w_lo > w_hi keeps none),
+ *   hops[v]  = length of a shortest root -> v path, -1 when none (int32[n]);
+ *   sigma[v] = number of shortest root -> v paths (double[n]; a path is a
+ *              sequence of entries, so a duplicated entry gives two paths;
+ *              sigma[root] = 1, 0 where unreached) -- the forward phase of
+ *              Brandes' betweenness algorithm.
+ * Counts are summed with double-precision atomic adds in no fixed order:
+ * exact while they stay below 2^53, otherwise within the rounding of the
+ * additions (relative error below about levels x max in-degree x 2^-53).
+ *
+ * row_off (int64[n+1]), col (int32[nnz]; may be NULL when nnz = 0), weight
+ * (int32[nnz] or NULL), hops and sigma are device pointers of ctx's GPU, in
+ * the caller's own numbering and entry order; anything else (host memory,
+ * another GPU) fails with BFS_ERR_INVALID_ARG before any device work.  The
+ * CSR is not modified and need not be uploaded; every row is checked
+ * against [0, nnz] and every kept column index against [0, n) before use,
+ * and a bad one ends the call with BFS_ERR_INVALID_GRAPH (outputs then
+ * undefined), never with an out-of-range access.  Scratch (about 24 bytes
+ * per vertex) comes from ctx's allocator -- its arena when it has one -- and
+ * is returned before the call returns.  The level loop is driven by the
+ * host: the call enqueues on `stream` and returns when the traversal is
+ * complete.  stats (nullable, host): levels, reached vertices, and the
+ * entries of the reached vertices' rows, kept or not (edges_scanned). */
+typedef struct bfs_paths_stats {
+    int64_t levels;         /* non-empty frontiers (max hops + 1) */
+    int64_t reached;        /* vertices with hops >= 0 */
+    int64_t edges_scanned;  /* entries of the reached vertices' rows */
+} bfs_paths_stats;
+bfs_status bfs_run_paths(bfs_context* ctx, const int64_t* row_off, const int32_t* col,
+                         const int32_t* weight, int64_t n, int64_t nnz, int32_t w_lo,
+                         int32_t w_hi, int32_t root, int32_t* hops, double* sigma, void* stream,
+                         bfs_paths_stats* stats);
+
 /* ---- traversal without device allocation ---------------------------------------
  * The paper has no counterpart to this entry point; it serves callers that
  * cannot allocate device memory at traversal time -- code that runs inside a

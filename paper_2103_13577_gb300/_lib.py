@@ -84,6 +84,11 @@ class LrbStats(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int64), ("kernels", ctypes.c_int64)]
 
 
+class PathsStats(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int64), ("reached", ctypes.c_int64),
+                ("edges_scanned", ctypes.c_int64)]
+
+
 class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("launches", ctypes.c_int64),
@@ -132,6 +137,8 @@ SIGNATURES = {
     "bfs_debug_set_barrier_test": (_i32, [_vp, _i32, _i64]),
     "bfs_debug_set_timeline": (_i32, [_vp, _vp, _i32]),
     "bfs_run_static": (_i32, [_vp, _vp, _i64, _i64, _i32, _vp, _vp, _vp, ctypes.POINTER(RunStats)]),
+    "bfs_run_paths": (_i32, [_vp, _vp, _vp, _vp, _i64, _i64, _i32, _i32, _i32, _vp, _vp, _vp,
+                             ctypes.POINTER(PathsStats)]),
 }
 
 _lib = None

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (BFS_DIST_INT8, BFS_OUT_HOST, BFS_TUNE_BATCHED, BFS_UPLOAD_DEVICE_PTRS,
-                   ButterflyStats, GraphInfo, LrbStats, RunStats, ServerStats, TuneResult, check)
+                   ButterflyStats, GraphInfo, LrbStats, PathsStats, RunStats, ServerStats,
+                   TuneResult, check)
 
 
 def _is_torch(x) -> bool:
@@ -37,7 +38,8 @@ def _buf(x, dtype: np.dtype | None = None):
             raise ValueError("tensor must be contiguous")
         if dtype is not None:
             want = {np.dtype(np.int32): "torch.int32", np.dtype(np.int64): "torch.int64",
-                    np.dtype(np.int8): "torch.int8", np.dtype(np.uint8): "torch.uint8"}[np.dtype(dtype)]
+                    np.dtype(np.int8): "torch.int8", np.dtype(np.uint8): "torch.uint8",
+                    np.dtype(np.float64): "torch.float64"}[np.dtype(dtype)]
             if str(x.dtype) != want:
                 raise TypeError(f"expected {want}, got {x.dtype}")
         return x.data_ptr(), x.is_cuda
@@ -170,6 +172,28 @@ def bfs_run_lrb(g: int, root: int, dist, stream=None) -> dict:
     check(_lib.lib().bfs_run_lrb(g, int(root), p_dist, _stream(stream), ctypes.byref(st)),
           "bfs_run_lrb")
     return {f: getattr(st, f) for f, _ in LrbStats._fields_}
+
+
+def bfs_run_paths(ctx: int, row_off, col, root: int, hops, sigma, weight=None, lo: int = 0,
+                  hi: int = 0, stream=None) -> dict:
+    """Shortest-path counts (hops int32, sigma float64) from `root` over the
+    entries e of a device CSR with lo <= weight[e] <= hi (every entry when
+    weight is None).  Device buffers only; returns the traversal
+    statistics."""
+    p_off, d_off = _buf(row_off, np.int64)
+    p_col, d_col = _buf(col, np.int32)
+    p_w, d_w = _buf(weight, np.int32)
+    p_h, d_h = _buf(hops, np.int32)
+    p_s, d_s = _buf(sigma, np.float64)
+    if not (d_off and d_col and d_h and d_s and (weight is None or d_w)):
+        raise ValueError("bfs_run_paths takes device buffers only")
+    n = row_off.shape[0] - 1
+    nnz = col.shape[0]
+    st = PathsStats()
+    check(_lib.lib().bfs_run_paths(ctx, p_off, p_col if nnz else None, p_w, n, nnz, int(lo),
+                                   int(hi), int(root), p_h, p_s, _stream(stream),
+                                   ctypes.byref(st)), "bfs_run_paths")
+    return {f: getattr(st, f) for f, _ in PathsStats._fields_}
 
 
 def bfs_butterfly_schedule(nodes: int, fanout: int, round_: int, node: int) -> list[int]:
@@ -313,6 +337,10 @@ class Context:
         if self.handle:
             bfs_context_destroy(self.handle)
             self.handle = None
+
+    def run_paths(self, row_off, col, root: int, hops, sigma, weight=None, lo: int = 0,
+                  hi: int = 0, stream=None) -> dict:
+        return bfs_run_paths(self.handle, row_off, col, root, hops, sigma, weight, lo, hi, stream)
 
     def memory(self) -> tuple[int, int]:
         used, cap = ctypes.c_size_t(), ctypes.c_size_t()

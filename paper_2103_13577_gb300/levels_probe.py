@@ -2,7 +2,7 @@
 16) and runs two single-source traversals with BFS_HOST_LOOP, so that each
 BFS level is its own kernel launch (one ncu result per level).
 
-  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent|do|timeline|batch]
+  python -m paper_2103_13577_gb300.levels_probe SCALE [hostloop|persistent|do|timeline|batch|paths]
 
 do: host-loop launches with the direction-optimizing mode.
 timeline: persistent launches with the level timeline attached; prints the
@@ -11,6 +11,8 @@ prefetch off and on, top-down and direction-optimizing.
 batch: four 64-root batched launches (int32 rows, top-down, persistent) on
 the roots the benchmark uses; prints the mean device time of the last two,
 the frontier sums and the algorithmic bytes of one launch.
+paths: two shortest-path-count traversals (bfs_run_paths, every entry kept)
+on the caller's CSR copied to the device; no graph upload.
 """
 from __future__ import annotations
 
@@ -31,6 +33,17 @@ def main():
     off, col = graphgen.kronecker(scale, 16, seed=22)
     roots = graphgen.pick_roots(off, 4, seed=3)
     ctx = bfs.Context(0)
+    if mode == "paths":
+        import numpy as np
+        n = len(off) - 1
+        d_off = torch.from_numpy(off).cuda()
+        d_col = torch.from_numpy(np.ascontiguousarray(col, dtype=np.int32)).cuda()
+        hops = torch.empty(n, dtype=torch.int32, device="cuda")
+        sigma = torch.empty(n, dtype=torch.float64, device="cuda")
+        for r in roots[:2]:
+            print(ctx.run_paths(d_off, d_col, int(r), hops, sigma), flush=True)
+        ctx.close()
+        return
     g = bfs.Graph(ctx, off, col)
     n = len(off) - 1
     if mode == "batch":
