@@ -193,7 +193,7 @@ def paths_measure(bfs, torch, dev_, stream, off, col, roots, n):
                      "levels_last_root": int(st["levels"]),
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "traffic": None,
-                                  "kernel": "paths_expand with paths_degrees and the scan",
+                                  "kernel": "paths_expand with paths_collect, paths_degrees and the scan",
                                   "algorithmic_bytes_per_traversal": float(nbytes.mean())}}
     pctx.close()
     del arena, d_off, d_col, d_w, hops, sigma

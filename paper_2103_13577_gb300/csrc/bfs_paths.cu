@@ -19,10 +19,11 @@
 //      search in the tile's span of the scan, so a hub's row spreads over
 //      many CTAs, light rows share one, and consecutive threads read
 //      consecutive columns.  A kept entry v -> u whose target has no
-//      distance claims it by compare-and-swap (the winner enqueues u);
-//      whenever the target's distance is level + 1, sigma[v] is added to
-//      sigma[u] by a double-precision atomic add.  sigma[v] is final when
-//      level L is expanded: every predecessor sits at level L - 1.
+//      distance, or already has level + 1, lies on a shortest path: it sets
+//      hops[u] = level + 1 and adds sigma[v] to sigma[u] by a
+//      double-precision atomic add.  sigma[v] is final when level L is
+//      expanded: every predecessor sits at level L - 1;
+//   4. the next frontier collected from the distances (hops = level + 1).
 // The host reads the next frontier size after each level.  Every column
 // index is checked against n and every row against nnz before use: a bad
 // CSR ends the call with BFS_ERR_INVALID_GRAPH, never an out-of-range
@@ -94,14 +95,21 @@ __device__ __forceinline__ long long owner_of(const int64_t* prefix, long long a
     return a;
 }
 
+// Level L's expansion.  A kept entry v -> u is a shortest-path edge exactly
+// when u has no distance yet or already has L + 1: the entry itself puts u
+// at L + 1.  So each such entry stores hops[u] = L + 1 (every writer stores
+// the same value) and adds sigma[v] to sigma[u] with an atomic whose result
+// is not used -- no compare-and-swap, no queue reservation, nothing a thread
+// waits for; the next frontier is collected afterwards (paths_collect).
+// Each thread takes 8 entries of the tile and issues their distance loads
+// together before the first update.
 __global__ void __launch_bounds__(kPathThreads)
 paths_expand(const int64_t* off, const int32_t* col, const int32_t* weight, int32_t lo, int32_t hi,
              long long n, const int32_t* fr, long long nfr, const int64_t* prefix, int level,
-             int32_t* hops, double* sigma, int32_t* next, PathCtl* ctl) {
+             int32_t* hops, double* sigma, PathCtl* ctl) {
     __shared__ long long s_span[2];
     const long long total = prefix[nfr];
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->edges += (unsigned long long)total;
-    const unsigned lane = threadIdx.x & 31u;
     const int32_t nxt_level = level + 1;
     for (long long t0 = (long long)blockIdx.x * kPathTile; t0 < total;
          t0 += (long long)gridDim.x * kPathTile) {
@@ -111,49 +119,62 @@ paths_expand(const int64_t* off, const int32_t* col, const int32_t* weight, int3
             s_span[threadIdx.x] = owner_of(prefix, 0, nfr - 1, threadIdx.x == 0 ? t0 : t1 - 1);
         __syncthreads();
         const long long first = s_span[0], last = s_span[1];
+        int32_t u[kPathPerThread];
+        double sv[kPathPerThread];
+        bool take[kPathPerThread];
+#pragma unroll
         for (int j = 0; j < kPathPerThread; ++j) {
             const long long e = t0 + (long long)j * kPathThreads + threadIdx.x;
-            bool take = false, win = false;
-            int32_t u = 0;
-            double sv = 0.0;
+            take[j] = false;
+            u[j] = 0;
+            sv[j] = 0.0;
             if (e < t1) {
                 const long long i = owner_of(prefix, first, last, e);
                 const int32_t v = fr[i];
                 const long long k = off[v] + (e - prefix[i]);
-                u = col[k];
-                take = weight == nullptr || (weight[k] >= lo && weight[k] <= hi);
-                if (take && (u < 0 || (long long)u >= n)) {
+                u[j] = col[k];
+                take[j] = weight == nullptr || (weight[k] >= lo && weight[k] <= hi);
+                if (take[j] && (u[j] < 0 || (long long)u[j] >= n)) {
                     ctl->bad = 1;
-                    take = false;
+                    take[j] = false;
                 }
-                if (take) sv = sigma[v];
+                if (take[j]) sv[j] = sigma[v];
             }
-            if (take) {
-                int32_t h = hops[u];
-                if (h == -1) {
-                    h = atomicCAS(hops + u, -1, nxt_level);
-                    if (h == -1) {
-                        win = true;
-                        h = nxt_level;
-                    }
-                }
-                if (h == nxt_level) atomicAdd(sigma + u, sv);
-            }
-            // winners enqueue u: one reservation per warp
-            const unsigned m = __ballot_sync(0xffffffffu, win);
-            if (m != 0u) {
-                const int leader = __ffs(m) - 1;
-                unsigned long long base = 0;
-                if ((int)lane == leader) base = atomicAdd(&ctl->tail, (unsigned long long)__popc(m));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
-                if (win) {
-                    if (slot < (unsigned long long)n) next[slot] = u;
-                    else ctl->bad = 1;
-                }
+        }
+        int32_t h[kPathPerThread];
+#pragma unroll
+        for (int j = 0; j < kPathPerThread; ++j) h[j] = take[j] ? hops[u[j]] : 0;
+#pragma unroll
+        for (int j = 0; j < kPathPerThread; ++j) {
+            if (take[j] && (h[j] == -1 || h[j] == nxt_level)) {
+                if (h[j] == -1) hops[u[j]] = nxt_level;
+                atomicAdd(sigma + u[j], sv[j]);
             }
         }
         __syncthreads();
+    }
+}
+
+// The next frontier: every vertex whose distance is `level`, in vertex order
+// within each warp (one queue reservation per warp).
+__global__ void paths_collect(const int32_t* hops, long long n, int32_t level, int32_t* next,
+                              PathCtl* ctl) {
+    const unsigned lane = threadIdx.x & 31u;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long nround = (n + 31) / 32 * 32;  // warp-uniform trip count
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
+        const bool in = v < n && hops[v] == level;
+        const unsigned m = __ballot_sync(0xffffffffu, in);
+        if (m == 0u) continue;
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if ((int)lane == leader) base = atomicAdd(&ctl->tail, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+        if (in) {
+            if (slot < (unsigned long long)n) next[slot] = (int32_t)v;
+            else ctl->bad = 1;
+        }
     }
 }
 
@@ -233,8 +254,8 @@ extern "C" bfs_status bfs_run_paths(bfs_context* ctx, const int64_t* row_off, co
         if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->tail, 0, sizeof(unsigned long long), s);
         if (e != cudaSuccess) break;
         paths_expand<<<sms * 8, kPathThreads, 0, s>>>(row_off, col, weight, w_lo, w_hi, n, fr[cur],
-                                                      nfr, prefix, level, hops, sigma, fr[cur ^ 1],
-                                                      ctl);
+                                                      nfr, prefix, level, hops, sigma, ctl);
+        paths_collect<<<sms * 8, 256, 0, s>>>(hops, n, level + 1, fr[cur ^ 1], ctl);
         e = cudaGetLastError();
         unsigned long long h_tail = 0;
         if (e == cudaSuccess)
