@@ -37,3 +37,11 @@ def test_null_arguments_are_rejected_without_a_gpu():
     assert lib.bfs_graph_free(None) == bfs.BFS_ERR_INVALID_ARG
     assert lib.bfs_poll(None, 1) == bfs.BFS_ERR_INVALID_ARG
     assert b"null" in lib.bfs_last_error()
+
+
+def test_paths_arguments_are_checked_without_a_gpu():
+    lib = bfs.load()
+    # no context, offsets or outputs: refused before any CUDA call
+    assert lib.bfs_run_paths(None, None, None, None, 4, 3, 0, 0, 0, None, None, None,
+                             None) == bfs.BFS_ERR_INVALID_ARG
+    assert b"paths" in lib.bfs_last_error()
