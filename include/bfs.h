@@ -412,26 +412,35 @@ bfs_status bfs_run_paths(bfs_context* ctx, const int64_t* row_off, const int32_t
  * routine.
  *
  * Same traversal as bfs_run, on a CSR the caller already holds on the
- * device: row_off (int64[n+1]), col (int32[nnz], 16-byte aligned; whole
- * 16-byte blocks are read, so the tail of the block holding the last entry
- * must be readable, as it is for any cudaMalloc or torch buffer), dist
- * (int32[n]) and parent (int32[n] or NULL) are device pointers on the
- * calling thread's current device; stream as for bfs_run.  The CSR is not
- * validated: every column index must lie in [0, n) and the offsets must not
- * decrease (check a graph once through bfs_graph_upload if in doubt).
+ * device: row_off (int64[n+1], 8-byte aligned), col (int32[nnz], 16-byte
+ * aligned; whole 16-byte blocks are read, so the tail of the block holding
+ * the last entry must be readable, as it is for any cudaMalloc or torch
+ * buffer), dist (int32[n]) and parent (int32[n] or NULL) are device pointers
+ * on the calling thread's current device; stream as for bfs_run.  Each call
+ * checks the CSR on the device before the traversal reads it (one extra pass
+ * over row_off and col): offsets must not decrease, row_off[0] >= 0,
+ * row_off[n] <= nnz, and every col[e] (0 <= e < nnz) must lie in [0, n).  A
+ * CSR that fails the check ends the traversal before any index is used and
+ * the call reports BFS_ERR_INVALID_GRAPH (dist and parent are then left as
+ * they were).
  *
  * Scratch: one fixed array of about 30 MB in the library's device code,
  * reserved on every GPU that loads the library and held until the process
  * exits; graphs are limited to n <= 524,288 vertices and nnz <= 33,554,432
- * entries, larger ones fail with BFS_ERR_UNSUPPORTED.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) and the
- * kernel's occupancy; make that first call before any stream capture.  All
- * calls share the one array and each call clears what must start at zero,
- * so calls whose work overlaps on the GPU (different streams, or different
- * host threads, without ordering between them) race and give undefined
- * results: order them on one stream.  With stats == NULL the call only
- * enqueues the work; with a host stats pointer it waits for the stream and
- * reports the traversal (BFS_ERR_TIMEOUT when a device-side wait expired). */
+ * entries, larger ones fail with BFS_ERR_UNSUPPORTED.  The first successful
+ * call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and the kernel's occupancy and keeps them for the process; make that first
+ * call before any stream capture (a failed set-up is not kept and is tried
+ * again by the next call), and do not call the function on a device after
+ * cudaDeviceReset there (the kept address would be stale).  All calls share
+ * the one array and each call clears what must start at zero, so calls
+ * whose work overlaps on the GPU (different streams, or different host
+ * threads, without ordering between them) race and give undefined results:
+ * order them on one stream.  With stats == NULL the call only enqueues the
+ * work and device-side failures (a failed CSR check, an expired wait) are
+ * not reported to the caller; pass a host stats pointer to have the call
+ * wait for the stream, report the traversal, and return BFS_ERR_INVALID_GRAPH
+ * or BFS_ERR_TIMEOUT when the device recorded one. */
 bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col, int64_t n, int64_t nnz,
                           int32_t root, int32_t* dist, int32_t* parent, void* stream,
                           bfs_run_stats* stats);

@@ -15,7 +15,8 @@ constexpr int64_t kMaxVertices = (1ll << 30) - 1;    // count field holds 30 bit
 constexpr int64_t kMaxEdges = (1ll << kCountShift) - 1;
 
 // Device status codes (mirrors of BFS_ERR_* that the kernels can raise).
-enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevOverflow = 2, kDevDepth = 3 };
+enum DevStatus : int { kDevOk = 0, kDevTimeout = 1, kDevOverflow = 2, kDevDepth = 3,
+                       kDevInvalidGraph = 4 };
 
 // One slot of the per-level control block; three slots rotate by level so
 // that the slot being written (next frontier), the slot being read (current
@@ -118,6 +119,9 @@ struct TraversalParams {
     int32_t timeline_cap;     // entries of timeline
     unsigned long long* timeline;  // nullable: %globaltimer after init, seed and each level
     unsigned long long graph_cond; // graph-captured loop: conditional handle of the while node
+    const int* pre_status;    // nullable: a status written by an earlier launch on the same
+                              // stream (CSR validation); non-zero ends the traversal before
+                              // its first access to the graph
 };
 
 // Direction of level L (Beamer, Asanovic, Patterson, "Direction-optimizing

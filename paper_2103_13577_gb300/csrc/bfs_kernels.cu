@@ -1446,6 +1446,13 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
     if (kStaged) tma_setup(P, S, s_dyn);
     const long long nthreads = (long long)gridDim.x * kBlock;
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
+    // a failed validation launch (same stream, so its result is visible to
+    // every CTA) ends the traversal before anything reads the graph
+    if (P.pre_status && ld_volatile_i32(P.pre_status) != 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) raise_status(P, ld_volatile_i32(P.pre_status));
+        kernel_exit(P);
+        return;
+    }
     stamp(P, 0);
     init_plain(P, tid, nthreads);
     if (grid_barrier(P)) {

@@ -3,11 +3,17 @@
 //
 // Everything the traversal needs besides the caller's CSR and outputs (the
 // visited bitmap, the two frontier queues of every degree bin with their
-// chunk tables, and the level/barrier/status control block) lives in one
-// file-scope __device__ array of fixed size, reserved when the library's
-// device code is loaded on a GPU and held until the process exits.  Host
-// code never touches that array by name: its device address is looked up
-// once per device with cudaGetSymbolAddress and passed to the kernel.
+// chunk tables, the level/barrier/status control block and the CSR check's
+// result word) lives in one file-scope __device__ array of fixed size,
+// reserved when the library's device code is loaded on a GPU and held until
+// the process exits.  Host code never touches that array by name: its device
+// address is looked up per device with cudaGetSymbolAddress and passed to the
+// kernels.
+//
+// Each call first checks the CSR on the device (offsets non-decreasing
+// inside [0, nnz], every column index inside [0, n)); the traversal kernel
+// reads the check's result before its first access to the graph and ends
+// at once when the check failed, so a bad index is never dereferenced.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -30,7 +36,8 @@ constexpr size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kCtlBytes = a256(3 * sizeof(LevelCtl));
 constexpr size_t kBarBytes = a256(sizeof(GridBarrier));
 constexpr size_t kStatBytes = a256(sizeof(DevStats));
-constexpr size_t kControlBytes = kCtlBytes + kBarBytes + kStatBytes;
+constexpr size_t kCheckBytes = a256(sizeof(int));   // the CSR check's result
+constexpr size_t kControlBytes = kCtlBytes + kBarBytes + kStatBytes + kCheckBytes;
 constexpr size_t kVisitedBytes = a256((size_t)(kStaticMaxVertices / 32 + 8) * 4);
 constexpr size_t kQueueEntries = (size_t)kStaticMaxVertices + 1;
 constexpr size_t kChunkCap1 = (size_t)(kStaticMaxEntries / kStaticChunkWarp) + 2;
@@ -49,26 +56,56 @@ static __device__ __align__(256) unsigned char g_bfs_static_scratch[bfs::kStatic
 namespace bfs {
 namespace {
 
+// Per-device set-up: the array's device address and the kernel's grid.  Only
+// a successful set-up is cached, so a first call that failed (for instance
+// one made during stream capture) is retried by the next call.
 struct StaticDevice {
-    std::once_flag once;
-    cudaError_t err = cudaSuccess;
+    std::mutex mu;
+    bool ready = false;
     unsigned char* scratch = nullptr;   // device address of g_bfs_static_scratch
     int grid = 0;
 };
 constexpr int kMaxDevices = 64;
 StaticDevice g_static_dev[kMaxDevices];
 
-void setup_device(StaticDevice& d) {
+cudaError_t setup_device(StaticDevice& d, int dev) {
+    std::lock_guard<std::mutex> lk(d.mu);
+    if (d.ready) return cudaSuccess;
     void* p = nullptr;
-    d.err = cudaGetSymbolAddress(&p, g_bfs_static_scratch);
-    if (d.err != cudaSuccess) return;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_bfs_static_scratch);
+    int sms = 0, nb = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, plain_persistent_fn(2), kBlock, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
     d.scratch = static_cast<unsigned char*>(p);
-    int dev = 0, sms = 0, nb = 0;
-    d.err = cudaGetDevice(&dev);
-    if (d.err == cudaSuccess) d.err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (d.err == cudaSuccess)
-        d.err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, plain_persistent_fn(2), kBlock, 0);
-    if (d.err == cudaSuccess) d.grid = nb * sms;
+    d.grid = nb * sms;
+    d.ready = true;
+    return cudaSuccess;
+}
+
+// The CSR check: every offset pair in order, the first offset >= 0, the last
+// <= nnz, every column index in [0, n).  Column indices are read 16 bytes at
+// a time (col is 16-byte aligned), the tail one by one.
+__global__ void static_csr_check(const int64_t* off, const int32_t* col, long long n,
+                                 long long nnz, int* status) {
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool bad = false;
+    if (tid == 0) bad = off[0] < 0 || off[n] > nnz;
+    for (long long v = tid; v < n; v += nthreads) bad |= off[v + 1] < off[v];
+    const long long n4 = nnz / 4;
+    const int4* c4 = reinterpret_cast<const int4*>(col);
+    for (long long i = tid; i < n4; i += nthreads) {
+        const int4 c = c4[i];
+        bad |= (c.x < 0) | (c.x >= n) | (c.y < 0) | (c.y >= n) | (c.z < 0) | (c.z >= n) |
+               (c.w < 0) | (c.w >= n);
+    }
+    for (long long e = 4 * n4 + tid; e < nnz; e += nthreads) bad |= col[e] < 0 || col[e] >= n;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(status, (int)kDevInvalidGraph);
 }
 
 }  // namespace
@@ -100,6 +137,10 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
         set_error("bfs_run_static: col must be 16-byte aligned");
         return BFS_ERR_INVALID_ARG;
     }
+    if (reinterpret_cast<uintptr_t>(row_off) & 7u) {
+        set_error("bfs_run_static: row_off must be 8-byte aligned");
+        return BFS_ERR_INVALID_ARG;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: cudaGetDevice");
@@ -108,8 +149,8 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
         return BFS_ERR_UNSUPPORTED;
     }
     StaticDevice& d = g_static_dev[dev];
-    std::call_once(d.once, setup_device, std::ref(d));
-    if (d.err != cudaSuccess) return cuda_fail(d.err, "bfs_run_static: per-device set-up");
+    e = setup_device(d, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: per-device set-up");
     if (d.grid < 1) {
         set_error("bfs_run_static: traversal kernel cannot be resident");
         return BFS_ERR_CUDA;
@@ -122,6 +163,8 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
     P.ctl = reinterpret_cast<LevelCtl*>(p);
     P.bar = reinterpret_cast<GridBarrier*>(p + kCtlBytes);
     P.stats = reinterpret_cast<DevStats*>(p + kCtlBytes + kBarBytes);
+    int* check = reinterpret_cast<int*>(p + kCtlBytes + kBarBytes + kStatBytes);
+    P.pre_status = check;
     p += kControlBytes;
     P.visited = reinterpret_cast<uint32_t*>(p);
     p += kVisitedBytes;
@@ -142,6 +185,8 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
         }
     }
     P.n = n;
+    P.nnz = nnz;
+    P.bu_limit = n;
     P.off = row_off;
     P.col = col;
     P.t_small = kStaticTSmall;
@@ -154,9 +199,13 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
     P.timeout_ns = 2000000000ll;
 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // the control block must start at zero; the kernel clears the bitmap
+    // the control block (with the check's result word) must start at zero;
+    // the traversal kernel clears the bitmap
     e = cudaMemsetAsync(d.scratch, 0, kControlBytes, s);
     if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: clearing the control block");
+    static_csr_check<<<d.grid, kBlock, 0, s>>>(row_off, nnz > 0 ? col : nullptr, n, nnz, check);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: CSR check launch");
     void* args[] = {&P};
     e = cudaLaunchCooperativeKernel(plain_persistent_fn(2), dim3(d.grid), dim3(kBlock), args, 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: cooperative launch");
@@ -174,8 +223,13 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
         set_error("bfs_run_static: device-side grid barrier wait timed out");
         return BFS_ERR_TIMEOUT;
     }
+    if (h.status == kDevInvalidGraph) {
+        set_error("bfs_run_static: CSR check failed (an offset decreases or lies outside "
+                  "[0, nnz], or a column index lies outside [0, n))");
+        return BFS_ERR_INVALID_GRAPH;
+    }
     if (h.status != kDevOk) {
-        set_error("bfs_run_static: device queue overflow (invalid CSR?)");
+        set_error("bfs_run_static: device queue overflow (internal error)");
         return BFS_ERR_CUDA;
     }
     return BFS_OK;
