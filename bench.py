@@ -146,11 +146,59 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def workload_config(n, m, world):
+    """The `config` of the JSON line: the workload only, identical for both
+    arms."""
+    return {"workload": WORKLOAD,
+            "graph": f"kronecker scale {SCALE} edge factor {EDGE_FACTOR} "
+                     "A/B/C=0.57/0.19/0.19, permuted, symmetric, deduplicated",
+            "vertices": int(n), "directed_entries": int(m), "roots": NROOTS,
+            "root_seed": ROOT_SEED, "graph_seed": GRAPH_SEED,
+            "l2": "inputs larger than L2 (column array %.0f MB > 129 MB)" % (m * 4 / 1e6),
+            "parallelism": f"replicas x{world}"}
+
+
 def make_workload(rank):
     import graphgen
     off, col = graphgen.kronecker(SCALE, EDGE_FACTOR, seed=GRAPH_SEED)
     roots = graphgen.pick_roots(off, NROOTS, seed=ROOT_SEED + 7919 * rank)
     return off, col, roots
+
+
+# ------------------------------------------- batched roofline numerator
+def batch_frontier_sums(rows, deg):
+    """Frontiers of a top-down 64-root batched traversal, recovered from its
+    distance rows: for every level L, |A_L| = the vertices some lane reaches
+    at level L (one queue entry each, carrying its lane set) and D_L = the
+    sum of their degrees (the column entries level L expands); plus R = the
+    vertices any lane reaches.  rows: [k][N] distances (-1 unreached, int32
+    or int8), deg: [N] out-degrees; torch tensors on one device."""
+    sizes, degs = [], []
+    top = int(rows.max().item())
+    for level in range(top + 1):
+        a = (rows == level).any(0)
+        sizes.append(int(a.sum().item()))
+        degs.append(int(deg[a].sum().item()))
+    reached = int((rows >= 0).any(0).sum().item())
+    return sizes, degs, reached
+
+
+def batch_algorithmic_bytes(sizes, degs, reached: int, n: int, k: int, elem: int) -> float:
+    """Bytes one top-down batched launch (bfs_batch_persistent) has to move,
+    each item once:
+      init      16 N                 visited/next lane-set pairs cleared
+      level L   4 D_L                column entries of the frontier's rows
+                + 28 |A_L|           two row offsets, queue entry (vertex + lane set)
+                + 16 N               sweep reads every vertex's lane-set pair
+                + 92 |A_L|           producing A_L: pair write-back, 64-byte
+                                     level row, queue entry
+      emit      12 N + 64 R          visited set and renumbering of every vertex,
+                                     level rows of the reached ones
+                + k N elem           the k distance rows
+    Lane-set updates of the neighbours (atomicOr on next) and the level-row
+    re-reads of vertices reached before are cache traffic, not counted."""
+    per_level = sum(4 * d + 120 * a + 16 * n for a, d in zip(sizes, degs))
+    return float(per_level + 16 * n + 12 * n + 64 * reached + k * n * elem)
 
 
 # ---------------------------------------------------------------- oracle
@@ -264,8 +312,7 @@ def reference_arm(args, rank, world):
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": WORKLOAD, "graph": f"kronecker scale {SCALE} edge factor {EDGE_FACTOR}",
-                   "vertices": len(off) - 1, "directed_entries": int(len(col)), "roots": NROOTS},
+        "config": workload_config(len(off) - 1, len(col), world),
         "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -362,7 +409,7 @@ def gpu_arm(args, rank, world, local_rank):
         g.run(int(r), h_dist, h_par)
     barrier()
     e2e_ms = np.zeros(NROOTS)
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = args.steps
     for _ in range(e2e_steps):
         for i, r in enumerate(roots):
             t0 = time.perf_counter()
@@ -431,10 +478,9 @@ def gpu_arm(args, rank, world, local_rank):
     batch_ms = bev[0].elapsed_time(bev[1]) / reps
     batch_gteps = bst["edges_scanned"] / (batch_ms * 1e-3) / 1e9
     # algorithmic bytes of the batched launch from its frontiers (the rows)
-    from paper_2103_13577_gb300 import profiling
     deg_dev = torch.from_numpy(np.diff(off)).to(dev_)
-    b_sizes, b_degs, b_reached = profiling.batch_frontier_sums(bd, deg_dev)
-    b_bytes = profiling.batch_algorithmic_bytes(b_sizes, b_degs, b_reached, n, NROOTS, 4)
+    b_sizes, b_degs, b_reached = batch_frontier_sums(bd, deg_dev)
+    b_bytes = batch_algorithmic_bytes(b_sizes, b_degs, b_reached, n, NROOTS, 4)
     del deg_dev
     g.set_option(bfs.BFS_OPT_DIRECTION, 1)
     g.run_batch(roots, bd, stream=stream)
@@ -471,15 +517,10 @@ def gpu_arm(args, rank, world, local_rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD,
-                       "graph": f"kronecker scale {SCALE} edge factor {EDGE_FACTOR} "
-                                "A/B/C=0.57/0.19/0.19, permuted, symmetric, deduplicated",
-                       "vertices": n, "directed_entries": int(len(col)), "roots": NROOTS,
-                       "root_seed": ROOT_SEED, "graph_seed": GRAPH_SEED,
-                       "bins": [info["t_small"], info["t_large"], info["chunk_warp"], info["chunk_cta"]],
-                       "relabelled": bool(info["relabelled"]),
-                       "l2": "inputs larger than L2 (column array %.0f MB > 129 MB)" % (len(col) * 4 / 1e6),
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(n, len(col), world),
+            "graph_setup": {"bins": [info["t_small"], info["t_large"], info["chunk_warp"],
+                                     info["chunk_cta"]],
+                            "relabelled": bool(info["relabelled"])},
             "aggregate_gteps": float(m_job.sum() / (t_job.sum() * 1e-3) / 1e9),
             "conventions": {
                 "trimmed_mean_gteps": trimmed_mean(m_job / (t_job * 1e-3) / 1e9, 0.1),
@@ -807,6 +848,112 @@ def large_arm(args):
     print(json.dumps(rec), flush=True)
 
 
+# ------------------------------------------------- profiling workloads
+def levels_arm(args):
+    """Small fixed workloads for ncu captures (no JSON line): a seeded
+    Kronecker graph of --levels-scale (edge factor 16, seed 22), roots as in
+    the headline workload.  --levels-mode:
+      hostloop    two single-source traversals with BFS_HOST_LOOP, so each
+                  level is its own kernel launch (one ncu result per level);
+      do          the same with the direction-optimizing mode;
+      persistent  two single-source traversals, device-side level loop;
+      timeline    persistent launches with the level timeline: the median
+                  time of init, seed and every level over 8 roots, top-down
+                  and direction-optimizing;
+      batch       four 64-root batched launches (int32 rows, top-down): the
+                  mean device time of the last two, the frontier sums and the
+                  algorithmic bytes of one launch;
+      paths       two shortest-path-count traversals (bfs_run_paths, every
+                  entry kept) on the caller's CSR copied to the device."""
+    import torch
+
+    import graphgen
+    import paper_2103_13577_gb300 as bfs
+
+    mode = args.levels_mode
+    off, col = graphgen.kronecker(args.levels_scale, 16, seed=GRAPH_SEED)
+    n = len(off) - 1
+    roots = graphgen.pick_roots(off, 4, seed=ROOT_SEED)
+    ctx = bfs.Context(0)
+    if mode == "paths":
+        d_off = torch.from_numpy(off).cuda()
+        d_col = torch.from_numpy(np.ascontiguousarray(col, dtype=np.int32)).cuda()
+        hops = torch.empty(n, dtype=torch.int32, device="cuda")
+        sigma = torch.empty(n, dtype=torch.float64, device="cuda")
+        for r in roots[:2]:
+            print(ctx.run_paths(d_off, d_col, int(r), hops, sigma), flush=True)
+        ctx.close()
+        return
+    g = bfs.Graph(ctx, off, col)
+    if mode == "batch":
+        rows = torch.empty((NROOTS, n), dtype=torch.int32, device="cuda")
+        broots = graphgen.pick_roots(off, NROOTS, seed=ROOT_SEED)
+        stream = torch.cuda.current_stream()
+        for _ in range(2):
+            g.run_batch(broots, rows, stream=stream)
+        g.batch_sync(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(2):
+            g.run_batch(broots, rows, stream=stream)
+        ev[1].record(stream)
+        st = g.batch_sync(stream)
+        ms = ev[0].elapsed_time(ev[1]) / 2
+        deg = torch.from_numpy(np.diff(off)).cuda()
+        sizes, degs, reached = batch_frontier_sums(rows, deg)
+        b = batch_algorithmic_bytes(sizes, degs, reached, n, NROOTS, 4)
+        print(json.dumps({"ms": ms, "levels": int(st["levels"]),
+                          "edges_scanned": int(st["edges_scanned"]), "frontier_entries": sizes,
+                          "frontier_edges": degs, "reached": reached, "algorithmic_bytes": b,
+                          "gbs": b / (ms * 1e-3) / 1e9}), flush=True)
+    else:
+        dist = torch.empty(n, dtype=torch.int32, device="cuda")
+        par = torch.empty(n, dtype=torch.int32, device="cuda")
+        if mode == "timeline":
+            level_timeline(bfs, g, graphgen.pick_roots(off, 8, seed=ROOT_SEED), dist, par)
+        else:
+            flags = bfs.BFS_HOST_LOOP if mode in ("hostloop", "do") else 0
+            if mode == "do":
+                g.set_option(bfs.BFS_OPT_DIRECTION, 1)
+            for r in roots[:2]:
+                g.run(int(r), dist, par, flags=flags)
+                print(g.sync(), flush=True)
+    g.close()
+    ctx.close()
+
+
+def level_timeline(bfs, g, roots, dist, par):
+    """Median %globaltimer gaps between init, seed and each level (persistent
+    launches, bfs_debug_set_timeline), top-down and direction-optimizing."""
+    import torch
+
+    stamps = torch.zeros(64, dtype=torch.int64, device="cuda")
+    bfs.bfs_debug_set_timeline(g.handle, stamps)
+    for direction in (0, 1):
+        g.set_option(bfs.BFS_OPT_DIRECTION, direction)
+        rows = []
+        for rep in range(2):
+            for r in roots:
+                stamps.zero_()
+                g.run(int(r), dist, par)
+                st = g.sync()
+                t = stamps.cpu().numpy()
+                k = 3 + st["levels"]
+                if rep == 1:
+                    rows.append(np.diff(t[:k]) / 1e3)
+        width = max(len(x) for x in rows)
+        a = np.full((len(rows), width), np.nan)
+        for i, x in enumerate(rows):
+            a[i, :len(x)] = x
+        med = np.nanmedian(a, axis=0)
+        tot = np.median([x.sum() for x in rows])
+        names = ["init", "seed"] + [f"L{i}" for i in range(width - 2)]
+        print(f"direction {direction} total_us {tot:.1f} " +
+              " ".join(f"{nm}={v:.1f}" for nm, v in zip(names, med)), flush=True)
+    g.set_option(bfs.BFS_OPT_DIRECTION, 0)
+    bfs.bfs_debug_set_timeline(g.handle, None)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -824,9 +971,14 @@ def main():
     ap.add_argument("--serve-budget", type=int, default=32, help="GiB")
     ap.add_argument("--large-scale", type=int, default=29)
     ap.add_argument("--large-ef", type=int, default=8)
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "serve", "large"],
+    ap.add_argument("--workload", default="plain",
+                    choices=["plain", "batched", "serve", "large", "levels"],
                     help="plain: the headline line (default); batched: the 64-root batched "
-                         "configuration on Kronecker and Erdos-Renyi graphs")
+                         "configuration on Kronecker and Erdos-Renyi graphs; serve: the query "
+                         "server; large: scale 29; levels: small fixed runs for ncu captures")
+    ap.add_argument("--levels-mode", default="hostloop",
+                    choices=["hostloop", "do", "persistent", "timeline", "batch", "paths"])
+    ap.add_argument("--levels-scale", type=int, default=22)
     ap.add_argument("--batch-scale", type=int, default=24)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -847,6 +999,10 @@ def main():
     if args.workload == "large":
         if rank == 0:
             large_arm(args)
+        return
+    if args.workload == "levels":
+        if rank == 0:
+            levels_arm(args)
         return
     if world > 1:
         import torch

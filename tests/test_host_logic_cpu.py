@@ -1,6 +1,7 @@
 """Host-side logic checked without a GPU: the level-direction rule the
 device and host loops share (compiled from the library's own header with
-the host compiler), and the ncu launch-list summariser behind profiles/."""
+the host compiler), and the benchmark's algorithmic-byte count of a batched
+launch (the numerator of its roofline)."""
 from __future__ import annotations
 
 import os
@@ -9,7 +10,7 @@ import textwrap
 
 import pytest
 
-from paper_2103_13577_gb300 import profiling
+import bench
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(HERE), "paper_2103_13577_gb300", "csrc")
@@ -54,32 +55,6 @@ def test_direction_rule(tmp_path):
     assert out[3].split() == ["0", "2"]        # 55555 * 18 < 1e6 <= 55556 * 18
 
 
-def test_launch_list_summary(tmp_path):
-    csv_path = tmp_path / "l.csv"
-    rows = ['"ID","Kernel Name","Metric Name","Metric Unit","Metric Value"']
-    for i in range(3):
-        rows.append(f'"{2 * i}","void bfs::bfs_plain_persistent<4, 0>(bfs::TraversalParams)",'
-                    f'"gpu__time_duration.sum","usecond","{500 + i}"')
-        rows.append(f'"{2 * i}","void bfs::bfs_plain_persistent<4, 0>(bfs::TraversalParams)",'
-                    f'"dram__bytes_read.sum","Mbyte","{700 + i}"')
-        rows.append(f'"{2 * i}","void bfs::bfs_plain_persistent<4, 0>(bfs::TraversalParams)",'
-                    f'"dram__bytes_write.sum","Mbyte","100"')
-        rows.append(f'"{2 * i + 1}","void bfs::rel_columns_kernel(int)","gpu__time_duration.sum",'
-                    f'"usecond","50"')
-    csv_path.write_text("==PROF== noise\n" + "\n".join(rows) + "\n")
-    md = tmp_path / "out.md"
-    js = tmp_path / "out.json"
-    profiling.summarize(str(csv_path), str(md), "bfs_plain_persistent", str(js), "cmd")
-    text = md.read_text()
-    assert "bfs::bfs_plain_persistent<4, 0>" in text or "bfs_plain_persistent<4, 0>" in text
-    assert "| 3 |" in text
-    import json
-    t = json.loads(js.read_text())
-    assert t["launches"] == 3
-    assert abs(t["dram_bytes_per_launch"] - 801e6) < 1e3
-    assert t["kernel_sha256_16"] == profiling.kernel_hash()
-
-
 def test_batch_frontier_sums_path_graph():
     # path 0-1-2-3-4, lanes rooted at both ends: level 3 holds 3 (lane 0)
     # and 1 (lane 1), so a vertex enters the frontier once per distinct level
@@ -87,11 +62,11 @@ def test_batch_frontier_sums_path_graph():
     rows = torch.tensor([[0, 1, 2, 3, 4], [4, 3, 2, 1, 0], [-1, -1, -1, -1, -1]],
                         dtype=torch.int8)
     deg = torch.tensor([1, 2, 2, 2, 1], dtype=torch.int64)
-    sizes, degs, reached = profiling.batch_frontier_sums(rows, deg)
+    sizes, degs, reached = bench.batch_frontier_sums(rows, deg)
     assert sizes == [2, 2, 1, 2, 2]
     assert degs == [2, 4, 2, 4, 2]
     assert reached == 5
-    b = profiling.batch_algorithmic_bytes(sizes, degs, reached, n=5, k=3, elem=1)
+    b = bench.batch_algorithmic_bytes(sizes, degs, reached, n=5, k=3, elem=1)
     # columns 4*14 + per-entry 120*9 + sweeps 16*5*5 + init/emit 28*5 + rows 64*5 + out 3*5
     assert b == 56 + 1080 + 400 + 140 + 320 + 15
 
@@ -100,5 +75,5 @@ def test_batch_frontier_sums_unreached_and_isolated():
     import torch
     rows = torch.tensor([[0, -1, 1], [1, -1, 0]], dtype=torch.int32)
     deg = torch.tensor([1, 0, 1], dtype=torch.int64)
-    sizes, degs, reached = profiling.batch_frontier_sums(rows, deg)
+    sizes, degs, reached = bench.batch_frontier_sums(rows, deg)
     assert sizes == [2, 2] and degs == [2, 2] and reached == 2
