@@ -15,11 +15,19 @@ code with it (the only common module is ``graphgen``, which makes inputs).
 * ``check_tree(off, col, root, dist, parent)`` -- Graph500-style checks of a
   BFS result that do not depend on which of several valid parents was
   chosen (used to accept GPU parents).
+* ``check_bfs(off, col, root, dist, parent=None)`` -- the same rules in
+  directed form plus a predecessor witness per reached vertex, streamed over
+  the CSR on all host cores (``bfs_check.c``): holds exactly when ``dist``
+  is the shortest-path hop count from ``root`` (and, with ``parent``, when
+  the parents form a valid BFS tree); used where the serial oracle is too
+  slow to run on every root (scale 29).
 
 Pins: ``tests/test_oracle_pins.py`` checks this oracle against Floyd-Warshall
 brute force, closed-form distances, scipy's breadth-first search, and
 union-find components; ``tests/test_oracle_paths_pins.py`` checks the path
-counts against walk counts from adjacency-matrix powers and closed forms.
+counts against walk counts from adjacency-matrix powers and closed forms;
+``tests/test_oracle_check_pins.py`` checks ``check_bfs`` by exhaustive
+enumeration of candidate distance and parent arrays on tiny graphs.
 """
 from __future__ import annotations
 
@@ -33,12 +41,18 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "bfs_oracle.c")
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_CHECK_SRC = os.path.join(_HERE, "bfs_check.c")
+_CHECK_PATH = os.path.join(_HERE, "libbfscheck.so")
 _lib = None
+_check_lib = None
 _lock = threading.Lock()
 
 
 def build(force: bool = False, src: str | None = None, out: str | None = None) -> str:
-    """Compile the oracle with plain gcc (no OpenMP, no vectorisation flags)."""
+    """Compile the oracle with plain gcc (no OpenMP, no vectorisation flags),
+    and the invariant checker (plain gcc with POSIX threads)."""
+    if src is None and out is None:
+        build_check(force)
     src = src or _SRC
     out = out or _LIB_PATH
     if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
@@ -46,6 +60,36 @@ def build(force: bool = False, src: str | None = None, out: str | None = None) -
         subprocess.check_call(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src])
         os.replace(tmp, out)
     return out
+
+
+def build_check(force: bool = False, src: str | None = None, out: str | None = None) -> str:
+    src = src or _CHECK_SRC
+    out = out or _CHECK_PATH
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-pthread", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, out)
+    return out
+
+
+def load_check(path: str | None = None):
+    """Load the invariant checker (the default build, or another compiled copy)."""
+    global _check_lib
+
+    def bind(lib):
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.oracle_check_bfs.argtypes = [ctypes.c_int64, i64p, i32p, ctypes.c_int64, i32p, i32p,
+                                         ctypes.c_int32, i64p, i64p, i64p, i64p]
+        lib.oracle_check_bfs.restype = ctypes.c_int64
+        return lib
+
+    if path is None:
+        with _lock:
+            if _check_lib is None:
+                _check_lib = bind(ctypes.CDLL(build_check()))
+        return _check_lib
+    return bind(ctypes.CDLL(path))
 
 
 def load(path: str | None = None):
@@ -203,3 +247,43 @@ def check_tree(off, col, root, dist, parent, undirected=True):
         if np.any(np.abs(du[both] - dv[both]) > 1):
             bad.append("edge spans more than one level")
     return bad
+
+
+CHECK_KINDS = ("root_dist", "below_minus_one", "reach_gap", "level_skip", "no_witness",
+               "root_parent", "unreached_parent", "bad_parent")
+
+
+def check_bfs(off, col, root, dist, parent=None, nthreads=None, lib=None):
+    """Certificate check of a BFS result (``bfs_check.c``): dist (int32 or
+    int8, -1 unreached) equals the hop distances from ``root`` exactly when
+    every count is zero; with ``parent`` the tree is checked too.  Returns a
+    dict: ``ok``, the violation count of each kind (``CHECK_KINDS``),
+    ``reached``, ``levels`` and ``edges_scanned`` (entries of the reached
+    rows).  The CSR itself must be valid (columns in [0, n))."""
+    lib = lib or load_check()
+    off, col = _csr(off, col)
+    n = len(off) - 1
+    if not (0 <= root < n):
+        raise ValueError("root out of range")
+    dist = np.ascontiguousarray(dist, dtype=np.int32)
+    if len(dist) != n:
+        raise ValueError("dist has the wrong length")
+    pp = None
+    if parent is not None:
+        parent = np.ascontiguousarray(parent, dtype=np.int32)
+        if len(parent) != n:
+            raise ValueError("parent has the wrong length")
+        pp = _p(parent, ctypes.c_int32)
+    bad = np.zeros(len(CHECK_KINDS), dtype=np.int64)
+    out = np.zeros(3, dtype=np.int64)
+    nt = int(nthreads or os.cpu_count() or 1)
+    rc = lib.oracle_check_bfs(n, _p(off, ctypes.c_int64), _p(col, ctypes.c_int32), int(root),
+                              _p(dist, ctypes.c_int32), pp, nt, _p(bad, ctypes.c_int64),
+                              _p(out[0:], ctypes.c_int64), _p(out[1:], ctypes.c_int64),
+                              _p(out[2:], ctypes.c_int64))
+    if rc < 0:
+        raise RuntimeError(f"oracle_check_bfs failed ({rc})")
+    res = {k: int(v) for k, v in zip(CHECK_KINDS, bad)}
+    res.update(ok=bool(rc == 0), reached=int(out[0]), levels=int(out[1]),
+               edges_scanned=int(out[2]))
+    return res
