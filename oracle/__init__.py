@@ -130,8 +130,10 @@ def _csr(off, col):
     return off, col
 
 
-def bfs(off, col, root, lib=None):
-    """Serial BFS from ``root``: (dist int32[n], parent int32[n], info)."""
+def bfs(off, col, root, lib=None, max_levels=None):
+    """Serial BFS from ``root``: (dist int32[n], parent int32[n], info).
+    ``max_levels`` bounds the per-level counts kept in ``info`` (default: as
+    many as the graph can have levels)."""
     lib = lib or load()
     off, col = _csr(off, col)
     n = len(off) - 1
@@ -139,7 +141,7 @@ def bfs(off, col, root, lib=None):
         raise ValueError("root out of range")
     dist = np.empty(n, dtype=np.int32)
     parent = np.empty(n, dtype=np.int32)
-    max_levels = n + 1
+    max_levels = n + 1 if max_levels is None else int(max_levels)
     levels = np.zeros(max_levels, dtype=np.int64)
     scanned = np.zeros(1, dtype=np.int64)
     nl = lib.oracle_bfs(n, _p(off, ctypes.c_int64), _p(col, ctypes.c_int32), int(root),
@@ -147,7 +149,8 @@ def bfs(off, col, root, lib=None):
                         _p(levels, ctypes.c_int64), max_levels, _p(scanned, ctypes.c_int64))
     if nl < 0:
         raise RuntimeError(f"oracle_bfs failed ({nl})")
-    info = {"levels": int(nl), "level_sizes": levels[:nl].copy(), "edges_scanned": int(scanned[0]),
+    info = {"levels": int(nl), "level_sizes": levels[:min(nl, max_levels)].copy(),
+            "edges_scanned": int(scanned[0]),
             "reached": int(np.count_nonzero(dist >= 0))}
     return dist, parent, info
 
