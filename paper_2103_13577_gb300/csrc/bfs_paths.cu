@@ -10,170 +10,363 @@
 // sigma[v] (the number of shortest root -> v paths) -- the forward phase of
 // Brandes' betweenness algorithm in its level-synchronous form.
 //
-// Per level:
-//   1. the out-degree of every frontier vertex (rows checked against nnz);
-//   2. an exclusive scan of those degrees (the frontier's entries laid end
-//      to end);
-//   3. an edge-balanced expansion: CTAs take tiles of 2048 consecutive
-//      frontier entries, each thread finds its entry's vertex by binary
-//      search in the tile's span of the scan, so a hub's row spreads over
-//      many CTAs, light rows share one, and consecutive threads read
-//      consecutive columns.  A kept entry v -> u whose target has no
-//      distance, or already has level + 1, lies on a shortest path: it sets
-//      hops[u] = level + 1 and adds sigma[v] to sigma[u] by a
-//      double-precision atomic add.  sigma[v] is final when level L is
+// One cooperative persistent launch runs the whole level loop; a grid
+// barrier (bounded by %globaltimer) separates its phases, so the host waits
+// once per traversal, not once per level.  Per level L:
+//   1. expansion: the frontier queue holds each vertex with the exclusive
+//      prefix of the frontier's degrees (its first entry's position in the
+//      level's entry sequence), so CTAs take tiles of 2048 consecutive
+//      entries; a chunk-start table (written when the vertices are queued)
+//      gives a tile's first and last queue entries, the span between them is
+//      staged in shared memory and each thread finds its entries' rows by
+//      binary search there, so a
+//      hub's row spreads over many CTAs, light rows share one, and
+//      consecutive threads read consecutive columns.  A kept entry v -> u
+//      lies on a shortest path exactly when u was not reached at level <= L
+//      (one bit of the visited bitmap, read without atomics: it does not
+//      change during the phase): such an entry marks u in the next-frontier
+//      bitmap and adds sigma[v] to sigma[u] (reductions whose results are not
+//      used, so nothing waits for them).  sigma[v] is final when level L is
 //      expanded: every predecessor sits at level L - 1;
-//   4. the next frontier collected from the distances (hops = level + 1).
-// The host reads the next frontier size after each level.  Every column
-// index is checked against n and every row against nnz before use: a bad
-// CSR ends the call with BFS_ERR_INVALID_GRAPH, never an out-of-range
-// access.
+//   2. collection: warps scan the next-frontier bitmap, give each marked
+//      vertex hops = L + 1, fold the bitmap into the visited one and clear
+//      it, and append the marked vertices with out-edges to the next queue
+//      -- one packed 64-bit atomicAdd per warp round reserves queue slots
+//      and the entry prefix together (count << 34 | entries) -- and mark in
+//      the chunk-start table every tile whose first entry they hold.
+// Every row is checked against [0, nnz] and every kept column index against
+// [0, n) before use: a bad CSR ends the call with BFS_ERR_INVALID_GRAPH,
+// never an out-of-range access.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "bfs_runtime.h"
 
 namespace bfs {
 
-cudaError_t exclusive_scan_i64(const int64_t* in, long long n, int64_t* out, int64_t* tmp,
-                               cudaStream_t s);
-
 namespace {
 
 constexpr int kPathThreads = 256;
-constexpr int kPathPerThread = 8;
-constexpr long long kPathTile = (long long)kPathThreads * kPathPerThread;  // entries per tile
+constexpr int kPathWarps = kPathThreads / 32;
+constexpr int kPathPerLane = 8;
+constexpr int kPathTile = 32 * kPathPerLane;                // entries per warp tile
+constexpr int kPathMinBlocks = 3;
+constexpr int kPackShift = 34;                              // count << 34 | entries
+constexpr unsigned long long kPackMask = (1ull << kPackShift) - 1ull;
 
 struct PathCtl {
-    unsigned long long tail;   // entries written to the next frontier
-    unsigned long long edges;  // entries of the expanded rows so far
-    int bad;                   // a row or column index out of range was met
-    int pad[3];
+    unsigned long long packed[2];   // queue of parity p: (entries << 34) | entry prefix
+    unsigned long long edges;       // entries of the reached rows
+    unsigned long long reached;     // vertices with hops >= 0
+    unsigned int bar_count, bar_gen, exit_count;
+    int bad;                        // a row or column index out of range was met
+    int status;                     // 1: a grid-barrier wait gave up
+    int abort;                      // tells waiting CTAs to leave
+    int levels;                     // max hops + 1
+    int pad;
 };
 
-__global__ void paths_init(int32_t* hops, double* sigma, long long n, int32_t root, int32_t* fr,
-                           PathCtl* ctl) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        hops[i] = i == root ? 0 : -1;
-        sigma[i] = i == root ? 1.0 : 0.0;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        fr[0] = root;
-        ctl->tail = 0;
-        ctl->edges = 0;
-        ctl->bad = 0;
-    }
+struct PathParams {
+    const int64_t* off;
+    const int32_t* col;
+    const int32_t* weight;          // nullable: every entry kept
+    int32_t lo, hi;
+    long long n, nnz;
+    int32_t root;
+    int32_t* hops;
+    double* sigma;
+    uint32_t* vis;                  // vertices reached at a level <= L
+    uint32_t* mark;                 // vertices reached at level L + 1 (being built)
+    int32_t* qv[2];                 // frontier vertices
+    int64_t* qe[2];                 // their first entry's position in the level's sequence
+    int64_t* qk[2];                 // row start minus that position: entry e of the sequence
+                                    // is col[e + qk] for the vertex holding it
+    int32_t* qc[2];                 // tile t's first queue entry: the one holding entry t * 256
+    long long qc_cap;               // slots of each qc array
+    PathCtl* ctl;
+    long long timeout_ns;
+};
+
+__device__ __forceinline__ unsigned long long timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// deg[i] = out-degree of frontier vertex fr[i]; a row outside [0, nnz]
-// counts as empty and raises the error flag.
-__global__ void paths_degrees(const int64_t* off, long long nnz, const int32_t* fr, long long nfr,
-                              int64_t* deg, PathCtl* ctl) {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nfr; i += stride) {
-        const int32_t v = fr[i];
-        const long long b = off[v], e = off[v + 1];
-        long long d = e - b;
-        if (b < 0 || d < 0 || e > nnz) {
-            ctl->bad = 1;
-            d = 0;
+// All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA
+// arrives on a counter; the last one bumps a generation word the others
+// poll.  A wait longer than timeout_ns records the failure and makes every
+// CTA leave; the return value says whether to go on.
+__device__ bool path_barrier(const PathParams& P) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        PathCtl* c = P.ctl;
+        int ok = 1;
+        const unsigned g = *(volatile unsigned*)&c->bar_gen;
+        __threadfence();
+        if (atomicAdd(&c->bar_count, 1u) + 1u == gridDim.x) {
+            c->bar_count = 0u;
+            __threadfence();
+            atomicExch(&c->bar_gen, g + 1u);
+        } else {
+            const unsigned long long t0 = timer_ns();
+            while (*(volatile unsigned*)&c->bar_gen == g) {
+                if (*(volatile int*)&c->abort) { ok = 0; break; }
+                if (timer_ns() - t0 > (unsigned long long)P.timeout_ns) {
+                    atomicExch(&c->status, 1);
+                    atomicExch(&c->abort, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
         }
-        deg[i] = d;
+        __threadfence();
+        if (*(volatile int*)&c->abort) ok = 0;
+        s_ok = ok;
     }
+    __syncthreads();
+    return s_ok != 0;
 }
 
-// Largest i in [a, b] with prefix[i] <= key (prefix[a] <= key required).
-__device__ __forceinline__ long long owner_of(const int64_t* prefix, long long a, long long b,
-                                             long long key) {
-    while (a < b) {
-        const long long m = (a + b + 1) >> 1;
-        if (prefix[m] <= key) a = m;
-        else b = m - 1;
-    }
-    return a;
-}
-
-// Level L's expansion.  A kept entry v -> u is a shortest-path edge exactly
-// when u has no distance yet or already has L + 1: the entry itself puts u
-// at L + 1.  So each such entry stores hops[u] = L + 1 (every writer stores
-// the same value) and adds sigma[v] to sigma[u] with an atomic whose result
-// is not used -- no compare-and-swap, no queue reservation, nothing a thread
-// waits for; the next frontier is collected afterwards (paths_collect).
-// Each thread takes 8 entries of the tile and issues their distance loads
-// together before the first update.
-__global__ void __launch_bounds__(kPathThreads)
-paths_expand(const int64_t* off, const int32_t* col, const int32_t* weight, int32_t lo, int32_t hi,
-             long long n, const int32_t* fr, long long nfr, const int64_t* prefix, int level,
-             int32_t* hops, double* sigma, PathCtl* ctl) {
-    __shared__ long long s_span[2];
-    const long long total = prefix[nfr];
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->edges += (unsigned long long)total;
-    const int32_t nxt_level = level + 1;
-    for (long long t0 = (long long)blockIdx.x * kPathTile; t0 < total;
-         t0 += (long long)gridDim.x * kPathTile) {
-        const long long t1 = t0 + kPathTile < total ? t0 + kPathTile : total;
-        // the frontier entries whose rows this tile covers: [s_span[0], s_span[1]]
-        if (threadIdx.x < 2)
-            s_span[threadIdx.x] = owner_of(prefix, 0, nfr - 1, threadIdx.x == 0 ? t0 : t1 - 1);
-        __syncthreads();
-        const long long first = s_span[0], last = s_span[1];
-        int32_t u[kPathPerThread];
-        double sv[kPathPerThread];
-        bool take[kPathPerThread];
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T x) {
+    const unsigned lane = threadIdx.x & 31u;
 #pragma unroll
-        for (int j = 0; j < kPathPerThread; ++j) {
-            const long long e = t0 + (long long)j * kPathThreads + threadIdx.x;
+    for (int d = 1; d < 32; d <<= 1) {
+        const T y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= (unsigned)d) x += y;
+    }
+    return x;
+}
+
+// Records, for every tile whose first entry falls in [eo, eo + deg), that
+// queue entry pos holds it (chunk-start table of the queue being built).
+__device__ __forceinline__ void mark_tiles(const PathParams& P, int nxt, long long pos, long long eo,
+                                           long long deg) {
+    const long long c0 = (eo + kPathTile - 1) / kPathTile, c1 = (eo + deg - 1) / kPathTile;
+    for (long long c = c0; c <= c1; ++c) {
+        if (c < P.qc_cap) P.qc[nxt][c] = (int32_t)pos;
+        else P.ctl->bad = 1;
+    }
+}
+
+// Level L's expansion over the queue of parity cur (cnt vertices, E entries).
+// Warps take tiles of 256 consecutive entries (round robin over the grid, no
+// CTA barriers): lane 0 reads the tile's first and last queue entries from
+// the chunk-start table, the warp stages that span (vertex, first entry
+// relative to the tile, row shift) in its shared-memory slice, and each lane
+// finds the row of its 8 entries (tile entries lane + 32 j) by a search that
+// starts at its previous entry's row.  Everything written during the launch
+// (queues, bitmaps, sigma) is read through L2 (ld.cg): an L1 or
+// read-only-cache copy could predate the write.
+__device__ void expand_paths(const PathParams& P, int cur, long long cnt, long long E) {
+    __shared__ int32_t s_rel[kPathWarps][kPathTile + 1];   // first tile entry of each span entry
+    __shared__ long long s_k[kPathWarps][kPathTile + 1];    // row shift
+    __shared__ int32_t s_v[kPathWarps][kPathTile + 1];
+    const unsigned lane = threadIdx.x & 31u;
+    const int w = threadIdx.x >> 5;
+    int32_t* const rel = s_rel[w];
+    long long* const ks = s_k[w];
+    int32_t* const vs = s_v[w];
+    const int32_t* qv = P.qv[cur];
+    const int64_t* qe = P.qe[cur];
+    const int64_t* qk = P.qk[cur];
+    const int32_t* qc = P.qc[cur];
+    const long long tiles = (E + kPathTile - 1) / kPathTile;
+    const long long nwarps = (long long)gridDim.x * kPathWarps;
+    for (long long t = (long long)blockIdx.x * kPathWarps + w; t < tiles; t += nwarps) {
+        const long long t0 = t * kPathTile;
+        const int len = (int)min((long long)kPathTile, E - t0);
+        // the tile's entries: from the one holding its first entry to the one
+        // holding the next tile's first entry (which may start exactly at the
+        // tile's end and then contributes nothing)
+        long long first = 0, last = 0;
+        if (lane == 0) {
+            first = min((long long)__ldcg(qc + t), cnt - 1);
+            last = t + 1 < tiles ? min((long long)__ldcg(qc + t + 1), cnt - 1) : cnt - 1;
+        }
+        first = __shfl_sync(0xffffffffu, first, 0);
+        last = __shfl_sync(0xffffffffu, last, 0);
+        // every queued vertex has edges: at most kPathTile + 1 entries
+        const int span = (int)max(0ll, min(last - first + 1, (long long)kPathTile + 1));
+        for (int i = (int)lane; i < span; i += 32) {
+            const long long eo = __ldcg(qe + first + i);
+            rel[i] = (int32_t)max(eo - t0, 0ll);
+            ks[i] = __ldcg(qk + first + i);
+            vs[i] = __ldcg(qv + first + i);
+        }
+        __syncwarp();
+        int32_t u[kPathPerLane];
+        int32_t v[kPathPerLane];
+        bool take[kPathPerLane];
+        int o = 0;
+#pragma unroll
+        for (int j = 0; j < kPathPerLane; ++j) {
+            const int r = j * 32 + (int)lane;   // tile entry
             take[j] = false;
             u[j] = 0;
-            sv[j] = 0.0;
-            if (e < t1) {
-                const long long i = owner_of(prefix, first, last, e);
-                const int32_t v = fr[i];
-                const long long k = off[v] + (e - prefix[i]);
-                u[j] = col[k];
-                take[j] = weight == nullptr || (weight[k] >= lo && weight[k] <= hi);
-                if (take[j] && (u[j] < 0 || (long long)u[j] >= n)) {
-                    ctl->bad = 1;
-                    take[j] = false;
+            v[j] = 0;
+            if (r < len) {
+                // rows are in order: search from the previous entry's row
+                if (o + 1 < span && rel[o + 1] <= r) {
+                    int a = o + 1, b = span - 1;
+                    while (a < b) {
+                        const int m = (a + b + 1) >> 1;
+                        if (rel[m] <= r) a = m;
+                        else b = m - 1;
+                    }
+                    o = a;
                 }
-                if (take[j]) sv[j] = sigma[v];
+                const long long k = t0 + r + ks[o];
+                v[j] = vs[o];
+                u[j] = __ldcs(P.col + k);
+                if (P.weight) {
+                    const int32_t wt = __ldcs(P.weight + k);
+                    take[j] = wt >= P.lo && wt <= P.hi;
+                } else {
+                    take[j] = true;
+                }
             }
         }
-        int32_t h[kPathPerThread];
+        uint32_t wd[kPathPerLane];
 #pragma unroll
-        for (int j = 0; j < kPathPerThread; ++j) h[j] = take[j] ? hops[u[j]] : 0;
+        for (int j = 0; j < kPathPerLane; ++j) {
+            if (take[j] && (u[j] < 0 || (long long)u[j] >= P.n)) {
+                P.ctl->bad = 1;
+                take[j] = false;
+            }
+            wd[j] = take[j] ? __ldcg(P.vis + (u[j] >> 5)) : 0xffffffffu;
+        }
 #pragma unroll
-        for (int j = 0; j < kPathPerThread; ++j) {
-            if (take[j] && (h[j] == -1 || h[j] == nxt_level)) {
-                if (h[j] == -1) hops[u[j]] = nxt_level;
-                atomicAdd(sigma + u[j], sv[j]);
+        for (int j = 0; j < kPathPerLane; ++j) {
+            if (take[j] && !((wd[j] >> (u[j] & 31)) & 1u)) {
+                atomicOr(P.mark + (u[j] >> 5), 1u << (u[j] & 31));
+                atomicAdd(P.sigma + u[j], __ldcg(P.sigma + v[j]));
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
 }
 
-// The next frontier: every vertex whose distance is `level`, in vertex order
-// within each warp (one queue reservation per warp).
-__global__ void paths_collect(const int32_t* hops, long long n, int32_t level, int32_t* next,
-                              PathCtl* ctl) {
+// Level L's collection into the queue of parity nxt.
+__device__ void collect_paths(const PathParams& P, int level, int nxt) {
     const unsigned lane = threadIdx.x & 31u;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long nround = (n + 31) / 32 * 32;  // warp-uniform trip count
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nround; v += stride) {
-        const bool in = v < n && hops[v] == level;
-        const unsigned m = __ballot_sync(0xffffffffu, in);
-        if (m == 0u) continue;
-        const int leader = __ffs(m) - 1;
-        unsigned long long base = 0;
-        if ((int)lane == leader) base = atomicAdd(&ctl->tail, (unsigned long long)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        const unsigned long long slot = base + (unsigned long long)__popc(m & ((1u << lane) - 1u));
-        if (in) {
-            if (slot < (unsigned long long)n) next[slot] = (int32_t)v;
-            else ctl->bad = 1;
+    const long long words = (P.n + 31) / 32;
+    const long long groups = (words + 31) / 32;
+    const long long nwarps = (long long)gridDim.x * (kPathThreads / 32);
+    long long found = 0;
+    for (long long gi = (long long)blockIdx.x * (kPathThreads / 32) + (threadIdx.x >> 5);
+         gi < groups; gi += nwarps) {
+        const long long w = gi * 32 + lane;
+        uint32_t word = 0u;
+        if (w < words) {
+            word = __ldcg(P.mark + w);
+            if (word) {
+                P.mark[w] = 0u;
+                P.vis[w] = __ldcg(P.vis + w) | word;
+            }
+        }
+        found += __popc(word);
+        while (__any_sync(0xffffffffu, word != 0u)) {
+            const bool has = word != 0u;
+            long long deg = 0, row = 0;
+            int32_t v = 0;
+            if (has) {
+                v = (int32_t)(w * 32 + __ffs(word) - 1);
+                word &= word - 1u;
+                P.hops[v] = level + 1;
+                const long long b = __ldg(P.off + v), e = __ldg(P.off + v + 1);
+                if (b < 0 || e < b || e > P.nnz) P.ctl->bad = 1;
+                else { deg = e - b; row = b; }
+            }
+            const unsigned long long x = deg > 0 ? (1ull << kPackShift) + (unsigned long long)deg : 0ull;
+            const unsigned long long incl = warp_incl_scan(x);
+            const unsigned long long tot = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned long long base = 0ull;
+            if (lane == 31 && tot != 0ull) base = atomicAdd(&P.ctl->packed[nxt], tot);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            if (deg > 0) {
+                const unsigned long long ex = incl - x;
+                const long long pos = (long long)(base >> kPackShift) + (long long)(ex >> kPackShift);
+                if (pos < P.n) {
+                    const long long eo = (long long)(base & kPackMask) + (long long)(ex & kPackMask);
+                    P.qv[nxt][pos] = v;
+                    P.qe[nxt][pos] = eo;
+                    P.qk[nxt][pos] = row - eo;
+                    mark_tiles(P, nxt, pos, eo, deg);
+                } else {
+                    P.ctl->bad = 1;
+                }
+            }
+        }
+    }
+    found = warp_incl_scan(found);
+    if (lane == 31 && found > 0) {
+        atomicAdd(&P.ctl->reached, (unsigned long long)found);
+        atomicMax(&P.ctl->levels, level + 2);
+    }
+}
+
+__global__ void __launch_bounds__(kPathThreads, kPathMinBlocks)
+paths_persistent(const __grid_constant__ PathParams P) {
+    const long long nthreads = (long long)gridDim.x * kPathThreads;
+    const long long tid = (long long)blockIdx.x * kPathThreads + threadIdx.x;
+    for (long long i = tid; i < P.n; i += nthreads) {
+        P.hops[i] = i == P.root ? 0 : -1;
+        P.sigma[i] = i == P.root ? 1.0 : 0.0;
+    }
+    const long long words = (P.n + 31) / 32;
+    for (long long i = tid; i < words; i += nthreads) {
+        P.vis[i] = 0u;
+        P.mark[i] = 0u;
+    }
+    if (path_barrier(P)) {
+        if (tid == 0) {
+            const int32_t r = P.root;
+            P.vis[r >> 5] = 1u << (r & 31);
+            const long long b = P.off[r], e = P.off[r + 1];
+            long long deg = 0;
+            if (b < 0 || e < b || e > P.nnz) P.ctl->bad = 1;
+            else deg = e - b;
+            if (deg > 0) {
+                P.qv[0][0] = r;
+                P.qe[0][0] = 0;
+                P.qk[0][0] = b;
+                mark_tiles(P, 0, 0, 0, deg);
+                P.ctl->packed[0] = (1ull << kPackShift) + (unsigned long long)deg;
+            }
+            P.ctl->reached = 1;
+            P.ctl->levels = 1;
+        }
+        bool ok = path_barrier(P);
+        for (int level = 0; ok; ++level) {
+            const int cur = level & 1, nxt = cur ^ 1;
+            const unsigned long long pk = __ldcg(&P.ctl->packed[cur]);
+            const long long cnt = min((long long)(pk >> kPackShift), P.n);
+            const long long E = (long long)(pk & kPackMask);
+            if (cnt == 0) break;
+            if (tid == 0) {
+                P.ctl->edges += (unsigned long long)E;
+                P.ctl->packed[nxt] = 0ull;   // last read at the start of level - 1
+            }
+            expand_paths(P, cur, cnt, E);
+            if (!path_barrier(P)) break;
+            collect_paths(P, level, nxt);
+            ok = path_barrier(P);
+        }
+    }
+    // last CTA out resets the barrier state for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&P.ctl->exit_count, 1u) + 1u == gridDim.x) {
+            P.ctl->exit_count = 0u;
+            P.ctl->bar_count = 0u;
+            P.ctl->abort = 0;
         }
     }
 }
@@ -207,10 +400,15 @@ extern "C" bfs_status bfs_run_paths(bfs_context* ctx, const int64_t* row_off, co
         set_error("paths: n must lie in [1, 2^31 - 1] and nnz must not be negative");
         return BFS_ERR_INVALID_ARG;
     }
+    if (nnz >= (1ll << kPackShift)) {
+        set_error("paths: nnz must be below 2^34");
+        return BFS_ERR_UNSUPPORTED;
+    }
     if (root < 0 || root >= n) {
         set_error("paths: root out of range");
         return BFS_ERR_ROOT_RANGE;
     }
+    TraceRange tr("bfs_run_paths", root);
     cudaError_t e = cudaSetDevice(ctx->device);
     if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
     const int dv = ctx->device;
@@ -219,63 +417,79 @@ extern "C" bfs_status bfs_run_paths(bfs_context* ctx, const int64_t* row_off, co
         set_error("paths: every array must be device memory of the context's GPU");
         return BFS_ERR_INVALID_ARG;
     }
+    int nb = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, paths_persistent, kPathThreads, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "paths: occupancy query");
+    if (nb < 1) {
+        set_error("paths: traversal kernel cannot be resident");
+        return BFS_ERR_CUDA;
+    }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceAllocator* m = ctx->mem;
     const size_t nz = (size_t)n;
-    int32_t* fr[2] = {static_cast<int32_t*>(m->alloc(nz * 4 + 64)),
-                      static_cast<int32_t*>(m->alloc(nz * 4 + 64))};
-    int64_t* deg = static_cast<int64_t*>(m->alloc(nz * 8 + 64));
-    int64_t* prefix = static_cast<int64_t*>(m->alloc(nz * 8 + 64));
-    int64_t* tmp = static_cast<int64_t*>(m->alloc((nz / 256 + 4) * 8));
-    PathCtl* ctl = static_cast<PathCtl*>(m->alloc(sizeof(PathCtl)));
+    const size_t words = (nz + 31) / 32 + 8;
+    PathParams P;
+    std::memset(&P, 0, sizeof(P));
+    const size_t tiles = (size_t)nnz / kPathTile + 2;
+    void* blk[11] = {m->alloc(nz * 4 + 64), m->alloc(nz * 4 + 64), m->alloc(nz * 8 + 64),
+                     m->alloc(nz * 8 + 64), m->alloc(words * 4), m->alloc(words * 4),
+                     m->alloc(sizeof(PathCtl)), m->alloc(tiles * 4), m->alloc(tiles * 4),
+                     m->alloc(nz * 8 + 64), m->alloc(nz * 8 + 64)};
     auto release = [&]() {
-        m->release(fr[0]);
-        m->release(fr[1]);
-        m->release(deg);
-        m->release(prefix);
-        m->release(tmp);
-        m->release(ctl);
+        for (void* b : blk) m->release(b);
     };
-    if (!fr[0] || !fr[1] || !deg || !prefix || !tmp || !ctl) {
-        release();
-        set_error("paths: device memory exhausted");
-        return BFS_ERR_NO_MEMORY;
+    for (void* b : blk)
+        if (!b) {
+            release();
+            set_error("paths: device memory exhausted");
+            return BFS_ERR_NO_MEMORY;
+        }
+    P.qv[0] = static_cast<int32_t*>(blk[0]);
+    P.qv[1] = static_cast<int32_t*>(blk[1]);
+    P.qe[0] = static_cast<int64_t*>(blk[2]);
+    P.qe[1] = static_cast<int64_t*>(blk[3]);
+    P.vis = static_cast<uint32_t*>(blk[4]);
+    P.mark = static_cast<uint32_t*>(blk[5]);
+    P.ctl = static_cast<PathCtl*>(blk[6]);
+    P.qc[0] = static_cast<int32_t*>(blk[7]);
+    P.qc[1] = static_cast<int32_t*>(blk[8]);
+    P.qk[0] = static_cast<int64_t*>(blk[9]);
+    P.qk[1] = static_cast<int64_t*>(blk[10]);
+    P.qc_cap = (long long)tiles;
+    P.off = row_off;
+    P.col = col;
+    P.weight = weight;
+    P.lo = w_lo;
+    P.hi = w_hi;
+    P.n = n;
+    P.nnz = nnz;
+    P.root = root;
+    P.hops = hops;
+    P.sigma = sigma;
+    P.timeout_ns = 2000000000ll;
+    e = cudaMemsetAsync(P.ctl, 0, sizeof(PathCtl), s);
+    if (e == cudaSuccess) {
+        void* args[] = {&P};
+        e = cudaLaunchCooperativeKernel((const void*)paths_persistent, dim3(nb * ctx->sms),
+                                        dim3(kPathThreads), args, 0, s);
     }
-    const int sms = ctx->sms;
-    paths_init<<<sms * 4, 256, 0, s>>>(hops, sigma, n, root, fr[0], ctl);
-    bfs_paths_stats st{};
-    long long nfr = 1, reached = 1;
-    int cur = 0;
-    for (int level = 0; nfr > 0 && e == cudaSuccess; ++level) {
-        st.levels = level + 1;
-        const int gd = (int)std::min<long long>((long long)sms * 8, (nfr + 255) / 256);
-        paths_degrees<<<gd, 256, 0, s>>>(row_off, nnz, fr[cur], nfr, deg, ctl);
-        e = exclusive_scan_i64(deg, nfr, prefix, tmp, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(&ctl->tail, 0, sizeof(unsigned long long), s);
-        if (e != cudaSuccess) break;
-        paths_expand<<<sms * 8, kPathThreads, 0, s>>>(row_off, col, weight, w_lo, w_hi, n, fr[cur],
-                                                      nfr, prefix, level, hops, sigma, ctl);
-        paths_collect<<<sms * 8, 256, 0, s>>>(hops, n, level + 1, fr[cur ^ 1], ctl);
-        e = cudaGetLastError();
-        unsigned long long h_tail = 0;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(&h_tail, &ctl->tail, sizeof(h_tail), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        nfr = (long long)std::min<unsigned long long>(h_tail, (unsigned long long)n);
-        reached += nfr;
-        cur ^= 1;
-    }
-    PathCtl h_ctl{};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&h_ctl, ctl, sizeof(h_ctl), cudaMemcpyDeviceToHost, s);
+    PathCtl h{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, P.ctl, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     release();
     if (e != cudaSuccess) return cuda_fail(e, "paths traversal");
-    if (h_ctl.bad) {
+    if (h.bad) {
         set_error("paths: a row offset or column index lies outside the CSR");
         return BFS_ERR_INVALID_GRAPH;
     }
-    st.reached = reached;
-    st.edges_scanned = (int64_t)h_ctl.edges;
-    if (stats) *stats = st;
+    if (h.status) {
+        set_error("paths: a device-side grid barrier wait timed out");
+        return BFS_ERR_TIMEOUT;
+    }
+    if (stats) {
+        stats->levels = h.levels;
+        stats->reached = (int64_t)h.reached;
+        stats->edges_scanned = (int64_t)h.edges;
+    }
     return BFS_OK;
 }

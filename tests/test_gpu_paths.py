@@ -7,7 +7,8 @@ level, reached and scanned-entry counts equal.  Kronecker, Erdos-Renyi and
 directed random graphs, weight filters (half the entries, one weight, an
 empty range), a grid whose counts pass 2^53, a hub row spread over many
 tiles, frontiers of degree-0 vertices, single-vertex and isolated-root
-graphs, an arena context, the scale-22 benchmark graph on sampled roots,
+graphs, an arena context, the benchmark's scale-22 workload (8 roots, both
+filters),
 and the error paths (bad CSR, host memory)."""
 from __future__ import annotations
 
@@ -196,9 +197,30 @@ def test_paths_rejects_host_memory(ctx):
     assert rc == bfs.BFS_ERR_ROOT_RANGE
 
 
-def test_paths_scale22_sampled_roots(ctx):
-    off, col = graphgen.kronecker(22, 16, seed=22)
-    roots = graphgen.pick_roots(off, 64, seed=3)
+def test_paths_scale22_bench_roots(ctx):
+    """The benchmark's path-count workload: the headline graph, its first 8
+    roots, every entry kept and weights 0-3 of uniform 0-7 kept."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from tests import fullsize as F
+    off, col = F.graph(F.KRON_S22)
+    roots = [int(r) for r in graphgen.pick_roots(off, 64, seed=F.ROOT_SEED)[:8]]
     w = weights_for(col, 5)
-    check(ctx, off, col, int(roots[0]))
-    check(ctx, off, col, int(roots[41]), w, 0, 3)
+    cases = [(r, None, 0, 0) for r in roots] + [(r, w, 0, 3) for r in roots]
+    with ThreadPoolExecutor(max_workers=8) as ex:
+        refs = list(ex.map(lambda c: oracle.bfs_paths(off, col, c[0], c[1], c[2], c[3]), cases))
+    d_off, d_col, d_w = dev(off, np.int64), dev(col, np.int32), dev(w, np.int32)
+    n = len(off) - 1
+    hops = torch.empty(n, dtype=torch.int32, device="cuda")
+    sigma = torch.empty(n, dtype=torch.float64, device="cuda")
+    for (r, wt, lo, hi), (eh, es, info) in zip(cases, refs):
+        st = ctx.run_paths(d_off, d_col, r, hops, sigma, None if wt is None else d_w, lo, hi)
+        assert np.array_equal(hops.cpu().numpy(), eh), (r, lo, hi)
+        sg = sigma.cpu().numpy()
+        exact = es < 2.0 ** 53
+        assert np.array_equal(sg[exact], es[exact]), (r, lo, hi)
+        if not exact.all():
+            tol = info["levels"] * int(np.bincount(col, minlength=n).max()) * 2.0 ** -52
+            assert np.allclose(sg[~exact], es[~exact], rtol=tol, atol=0.0)
+        assert (st["levels"], st["reached"], st["edges_scanned"]) == \
+            (info["levels"], info["reached"], info["edges_scanned"])
