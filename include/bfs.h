@@ -263,10 +263,17 @@ bfs_status bfs_batch_sync(bfs_graph* g, void* stream, bfs_run_stats* stats);
  * graph's own options, e.g. BFS_OPT_DIRECTION).  Launches run on num_streams CUDA
  * streams so work from different graphs overlaps on the device.  A launch is
  * admitted only while the device memory of all launches in flight stays
- * within memory_budget bytes; queries that do not fit wait.  A query whose
+ * within memory_budget bytes, and, next to launches whose kernels are still
+ * running, only while one CTA of each fits on one SM together (each such
+ * launch then runs one CTA per SM; a launch made while nothing else runs
+ * gets the whole grid): every persistent grid is then resident at once and
+ * none waits on another's SMs.  Queries that do not fit wait.  A query whose
  * smallest launch alone exceeds the budget fails with BFS_ERR_BUDGET.
  * dist_out (host, int32[n]) is written when the query completes; the pointer
- * must stay valid until then. */
+ * must stay valid until then.  Give pinned memory (cudaHostAlloc or a pinned
+ * torch tensor): a copy into pageable memory is synchronous, so the
+ * dispatcher would wait for each launch to finish before taking the next
+ * queries, and nothing would overlap. */
 bfs_status bfs_server_create(bfs_context* ctx, size_t memory_budget, int32_t num_streams,
                              bfs_server** out);
 bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id);
@@ -303,13 +310,29 @@ bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out);
  * one to come back if none is free (a buffer returns when its query
  * completes).  On return (every query done) done_ns[i] is the query's
  * completion time on the server's clock, status_out[i] its status and, when
- * slot_out is not NULL, slot_out[i] the buffer it used.  Waits inside are
+ * slot_out is not NULL, slot_out[i] the buffer it used.  Each graph's
+ * queries are submitted by a thread of their own, so a graph whose buffers
+ * are all in use delays only its own later queries.  Waits inside are
  * bounded by timeout_us per query (negative: none). */
 bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids,
                              const int32_t* roots, const int64_t* arrival_ns,
                              int32_t* const* graph_bufs, const int32_t* bufs_per_graph,
                              int64_t timeout_us, int64_t* done_ns, int32_t* status_out,
                              int32_t* slot_out);
+/* The one-at-a-time baseline of a served trace: query i (graph
+ * graphs[graph_ids[i]], root roots[i]) runs as bfs_run with a host output
+ * row (BFS_OUT_HOST on `stream`) once arrival_ns[i] has come, strictly in
+ * arrival order, from the calling thread -- each query waits for every
+ * earlier one, as repeated plain single-source traversals on one GPU do.
+ * Rows go to graph_bufs[g] (bufs_per_graph[g] consecutive rows of n_g int32,
+ * used round robin).  done_ns[i] is the time bfs_run returned (steady
+ * clock, as bfs_ticket_times), status_out[i] its status.  Returns the first
+ * failure, if any. */
+bfs_status bfs_replay_single(bfs_graph* const* graphs, int32_t ngraphs, int64_t nq,
+                             const int32_t* graph_ids, const int32_t* roots,
+                             const int64_t* arrival_ns, int32_t* const* graph_bufs,
+                             const int32_t* bufs_per_graph, void* stream, int64_t* done_ns,
+                             int32_t* status_out);
 /* Stops the server; queued queries finish with BFS_ERR_CANCELLED. */
 bfs_status bfs_server_destroy(bfs_server* s);
 
@@ -386,12 +409,15 @@ bfs_status bfs_run_lrb(bfs_graph* g, int32_t root, int32_t* dist, void* stream,
  * CSR is not modified and need not be uploaded; every row is checked
  * against [0, nnz] and every kept column index against [0, n) before use,
  * and a bad one ends the call with BFS_ERR_INVALID_GRAPH (outputs then
- * undefined), never with an out-of-range access.  Scratch (about 24 bytes
- * per vertex) comes from ctx's allocator -- its arena when it has one -- and
- * is returned before the call returns.  The level loop is driven by the
- * host: the call enqueues on `stream` and returns when the traversal is
- * complete.  stats (nullable, host): levels, reached vertices, and the
- * entries of the reached vertices' rows, kept or not (edges_scanned). */
+ * undefined), never with an out-of-range access.  nnz must be below
+ * 2^34 (BFS_ERR_UNSUPPORTED otherwise).  Scratch (about 40.3 bytes per
+ * vertex) comes from ctx's allocator -- its arena when it has one -- and is
+ * returned before the call returns.  The whole level loop runs in one
+ * cooperative launch on `stream` (grid barriers between its phases, each
+ * wait bounded; BFS_ERR_TIMEOUT when one gives up); the call then waits for
+ * the stream and returns when the traversal is complete.  stats (nullable,
+ * host): levels, reached vertices, and the entries of the reached vertices'
+ * rows, kept or not (edges_scanned). */
 typedef struct bfs_paths_stats {
     int64_t levels;         /* non-empty frontiers (max hops + 1) */
     int64_t reached;        /* vertices with hops >= 0 */

@@ -130,6 +130,7 @@ SIGNATURES = {
                                 ctypes.POINTER(_i64)]),
     "bfs_server_get_stats": (_i32, [_vp, ctypes.POINTER(ServerStats)]),
     "bfs_server_replay": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
+    "bfs_replay_single": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "bfs_server_destroy": (_i32, [_vp]),
     "bfs_last_error": (ctypes.c_char_p, []),
     "bfs_status_string": (ctypes.c_char_p, [_i32]),

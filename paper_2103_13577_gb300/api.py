@@ -322,6 +322,38 @@ def bfs_server_replay(s: int, graph_ids, roots, arrival_ns, graph_bufs, timeout_
     return done, status, slot
 
 
+def bfs_replay_single(graphs, graph_ids, roots, arrival_ns, graph_bufs, stream=None):
+    """The one-at-a-time baseline of a served trace (see include/bfs.h):
+    query i runs as bfs_run with a host output row once its arrival time has
+    come, in arrival order, from a native thread.  graphs: graph handles;
+    graph_bufs: one C-contiguous int32 host array [k_g, n_g] per graph, used
+    round robin.  Returns (done_ns, status) arrays."""
+    gid = np.ascontiguousarray(graph_ids, dtype=np.int32)
+    rts = np.ascontiguousarray(roots, dtype=np.int32)
+    arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
+    nq = len(gid)
+    if len(rts) != nq or len(arr) != nq or len(graph_bufs) != len(graphs):
+        raise ValueError("graph_ids, roots and arrival_ns must have the same length, "
+                         "and one buffer array per graph")
+    hs = (ctypes.c_void_p * len(graphs))(*graphs)
+    ptrs = (ctypes.c_void_p * len(graph_bufs))()
+    counts = np.zeros(len(graph_bufs), dtype=np.int32)
+    for i, b in enumerate(graph_bufs):
+        p, dev = _buf(b, np.int32)
+        if dev:
+            raise ValueError("replay buffers are host memory")
+        ptrs[i] = p
+        counts[i] = b.shape[0]
+    done = np.zeros(nq, dtype=np.int64)
+    status = np.zeros(nq, dtype=np.int32)
+    check(_lib.lib().bfs_replay_single(ctypes.cast(hs, ctypes.c_void_p), len(graphs), nq,
+                                       gid.ctypes.data, rts.ctypes.data, arr.ctypes.data,
+                                       ctypes.cast(ptrs, ctypes.c_void_p), counts.ctypes.data,
+                                       _stream(stream), done.ctypes.data, status.ctypes.data),
+          "bfs_replay_single")
+    return done, status
+
+
 def bfs_server_destroy(s: int) -> None:
     check(_lib.lib().bfs_server_destroy(s), "bfs_server_destroy")
 

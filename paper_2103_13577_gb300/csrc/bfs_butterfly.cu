@@ -159,6 +159,7 @@ extern "C" bfs_status bfs_butterfly_schedule(int32_t nodes, int32_t fanout, int3
 
 extern "C" bfs_status bfs_run_butterfly(bfs_graph* g, int32_t root, int32_t nodes, int32_t fanout,
                                         int32_t* dist, void* stream, bfs_butterfly_stats* stats) {
+    TraceRange tr("bfs_run_butterfly", root);
     if (!g || !dist) {
         set_error("butterfly: null graph or dist");
         return BFS_ERR_INVALID_ARG;
@@ -242,6 +243,7 @@ extern "C" bfs_status bfs_run_butterfly(bfs_graph* g, int32_t root, int32_t node
     std::vector<unsigned long long> h_ql(nodes), h_qg(nodes);
     int cur = 0;
     for (int level = 0; e == cudaSuccess; ++level) {
+        TraceRange lv("level", level);
         e = cudaMemcpyAsync(h_ql.data(), ql_cnt[cur], nodes * 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) break;

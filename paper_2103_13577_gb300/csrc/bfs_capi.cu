@@ -501,6 +501,7 @@ bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist
         prev_bu = dir == 2;
         P.level = level;
         P.dir_override = dir;
+        TraceRange lv("level", level);
         if ((st = launch_plain_kernel(fn, g->grid_plain, P, s, smem)) != BFS_OK) return st;
         if ((st = read_ctl(ws, (level + 1) % 3, &c, s)) != BFS_OK) return st;
         if (ctl_empty(c)) {
@@ -535,6 +536,7 @@ bfs_status run_batch_on(bfs_graph* g, Workspace* ws, const int32_t* roots, int32
             return fail(BFS_ERR_DEPTH_OVERFLOW, "int8 distances: level above 126");
         P.level = level;
         P.phase = 2;
+        TraceRange lv("level", level);
         if ((st = launch_plain_kernel(batch_step_fn(g->min_blocks), grid, P, s)) != BFS_OK) return st;
         P.phase = 3;
         if ((st = launch_plain_kernel(batch_step_fn(g->min_blocks), grid, P, s)) != BFS_OK) return st;
@@ -573,6 +575,20 @@ bfs_status batch_finish(bfs_graph* g, Workspace* ws, cudaStream_t s, bfs_run_sta
 }
 
 int32_t plain_grid_of(const bfs_graph* g) { return g->grid_plain; }
+
+bfs_status cta_footprint(const bfs_graph* g, bool batched, CtaFootprint* out) {
+    const void* fn = batched ? batch_persistent_fn(g->min_blocks)
+                             : plain_persistent_fn(g->min_blocks, g->tma_stage != 0);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    // registers are allocated per warp in units of 256
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+    out->regs = warp_regs * (kBlock / 32);
+    out->threads = kBlock;
+    out->smem = fa.sharedSizeBytes + (batched ? 0 : plain_smem(g));
+    return BFS_OK;
+}
 
 static bfs_status ensure_workspace(bfs_graph* g, bool batched, cudaStream_t s, Workspace** out) {
     Workspace*& slot = batched ? g->ws_batch : g->ws_plain;
@@ -679,6 +695,7 @@ static bfs_status compute_bins(bfs_graph* g, cudaStream_t s) {
 bfs_status bfs_graph_upload(bfs_context* ctx, const int64_t* row_off, const int32_t* col,
                             int64_t n, int64_t nnz, uint32_t flags, void* stream,
                             bfs_graph** out) {
+    TraceRange tr("bfs_graph_upload", n);
     if (!ctx || !row_off || !out || (!col && nnz > 0))
         return fail(BFS_ERR_INVALID_ARG, "null argument");
     *out = nullptr;
@@ -855,6 +872,7 @@ bfs_status bfs_graph_set_bins(bfs_graph* g, int32_t t_small, int32_t t_large, in
 
 bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* dist, int32_t* parent, void* stream,
                    uint32_t flags) {
+    TraceRange tr("bfs_run", root);
     if (!g || !dist) return fail(BFS_ERR_INVALID_ARG, "null graph or dist");
     if (flags & ~(BFS_OUT_HOST | BFS_HOST_LOOP | BFS_GRAPH_LOOP))
         return fail(BFS_ERR_INVALID_ARG, "unknown flag");
@@ -899,6 +917,7 @@ bfs_status bfs_graph_sync(bfs_graph* g, void* stream, bfs_run_stats* stats) {
 
 bfs_status bfs_run_batch(bfs_graph* g, const int32_t* roots, int32_t k, void* dist, void* stream,
                          uint32_t flags) {
+    TraceRange tr("bfs_run_batch", k);
     if (!g || !roots || !dist) return fail(BFS_ERR_INVALID_ARG, "null argument");
     if (k < 1 || k > 64) return fail(BFS_ERR_INVALID_ARG, "k must be in 1..64");
     if (flags & ~(BFS_OUT_HOST | BFS_DIST_INT8 | BFS_HOST_LOOP | BFS_GRAPH_LOOP))

@@ -119,6 +119,7 @@ using namespace bfs;
 
 extern "C" bfs_status bfs_run_lrb(bfs_graph* g, int32_t root, int32_t* dist, void* stream,
                                   bfs_lrb_stats* stats) {
+    TraceRange tr("bfs_run_lrb", root);
     if (!g || !dist) {
         set_error("lrb: null graph or dist");
         return BFS_ERR_INVALID_ARG;
@@ -176,6 +177,7 @@ extern "C" bfs_status bfs_run_lrb(bfs_graph* g, int32_t root, int32_t* dist, voi
     long long nfr = 1;
     int cur = 0;
     for (int level = 0; nfr > 0 && e == cudaSuccess; ++level) {
+        TraceRange lv("level", level);
         st.levels = level + 1;
         // bin the frontier by log2(degree)
         e = cudaMemsetAsync(cnt, 0, 3 * kLrbBins * 8, s);

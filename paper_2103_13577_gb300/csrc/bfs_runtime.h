@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <atomic>
 #include <cstdint>
@@ -106,6 +107,32 @@ struct bfs_graph {
 };
 
 namespace bfs {
+// NVTX range in the library's own domain ("bfs"), with an integer payload
+// (root, lane count, level ...): the host side of every traversal, upload,
+// tuning trial, host-driven level and server launch shows up by name on an
+// Nsight timeline.  With no tool attached a push/pop is a pointer test.
+class TraceRange {
+public:
+    TraceRange(const char* name, int64_t payload = 0) {
+        static nvtxDomainHandle_t dom = nvtxDomainCreateA("bfs");
+        domain_ = dom;
+        nvtxEventAttributes_t a = {};
+        a.version = NVTX_VERSION;
+        a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+        a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+        a.message.ascii = name;
+        a.payloadType = NVTX_PAYLOAD_TYPE_INT64;
+        a.payload.llValue = payload;
+        nvtxDomainRangePushEx(domain_, &a);
+    }
+    ~TraceRange() { nvtxDomainRangePop(domain_); }
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+
+private:
+    nvtxDomainHandle_t domain_;
+};
+
 // helpers shared by the C ABI translation units
 void set_error(const std::string& msg);
 bfs_status cuda_fail(cudaError_t e, const char* what);
@@ -119,4 +146,12 @@ bfs_status batch_finish(bfs_graph* g, Workspace* ws, cudaStream_t stream, bfs_ru
 bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist, int32_t* parent,
                         cudaStream_t stream, uint32_t flags, int32_t grid);
 int32_t plain_grid_of(const bfs_graph* g);
+// Resources one CTA of g's persistent traversal kernel holds on an SM
+// (registers, threads, shared memory), for launches that share the GPU.
+struct CtaFootprint {
+    int regs = 0;
+    int threads = 0;
+    size_t smem = 0;
+};
+bfs_status cta_footprint(const bfs_graph* g, bool batched, CtaFootprint* out);
 }  // namespace bfs

@@ -12,8 +12,10 @@
 // records an event.  Completed events release the memory, which admits
 // the next launch -- so queries that arrive while others are on the GPU
 // join the next launch on a free slot, and launches on different slots
-// overlap on the device (each launch's persistent grid is sized to a share
-// of the SMs so several can be resident together).
+// overlap on the device: a launch made while others are in flight gets one
+// CTA per SM and is admitted only while the CTAs of all launches in flight
+// fit one SM side by side (registers, threads, shared memory), so every
+// persistent grid is resident at once and none waits on another's SMs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,6 +50,8 @@ struct Launch {
     int slot = -1;
     int32_t graph_id = 0;
     bool plain = false;      // k single-source traversals instead of one batched launch
+    int ctas_per_sm = 0;     // resident CTAs of its kernel on every SM
+    CtaFootprint cta;        // what one of them holds
     Workspace* ws = nullptr;
     void* d_dist = nullptr;
     std::vector<std::shared_ptr<Query>> lanes;
@@ -65,7 +69,8 @@ struct GraphPolicy {
 
 struct SlotState {
     cudaStream_t stream = nullptr;
-    cudaEvent_t event = nullptr;
+    cudaEvent_t event = nullptr;     // the launch's kernels and result copies are done
+    cudaEvent_t kevent = nullptr;    // its kernels are done (the SMs are free again)
     bool busy = false;
 };
 
@@ -93,6 +98,10 @@ struct bfs_server {
     size_t rr = 0;
     bfs_server_stats stats{};
     size_t inflight_bytes = 0;
+    // one SM's resources: launches in flight together must fit in them
+    // side by side, or their persistent grids could wait on each other
+    int sm_regs = 0, sm_threads = 0;
+    size_t sm_smem = 0;
 };
 
 namespace bfs {
@@ -122,12 +131,35 @@ static bool try_launch(bfs_server* s) {
         SlotState& sl = s->slots[free_slot];
         bfs_status st = BFS_OK;
         cudaSetDevice(s->ctx->device);
+        // A cooperative launch is only guaranteed to be resident by itself.
+        // Alone it takes the whole grid; next to others it takes one CTA per
+        // SM, and only while every launch in flight fits one SM together
+        // (two launches that each got part of their grid would wait on each
+        // other's SMs at their grid barriers).
+        CtaFootprint fp;
+        if (cta_footprint(g, !plain, &fp) != BFS_OK) continue;
+        const bool alone = s->inflight.empty();
+        if (!alone) {
+            long long regs = fp.regs, threads = fp.threads;
+            size_t smem = fp.smem;
+            for (const Launch& o : s->inflight) {
+                // a launch whose kernels are done holds no SM resources while
+                // its result copies run
+                if (cudaEventQuery(s->slots[o.slot].kevent) == cudaSuccess) continue;
+                cudaGetLastError();
+                regs += (long long)o.ctas_per_sm * o.cta.regs;
+                threads += (long long)o.ctas_per_sm * o.cta.threads;
+                smem += (size_t)o.ctas_per_sm * o.cta.smem;
+            }
+            if (regs > s->sm_regs || threads > s->sm_threads || smem > s->sm_smem) continue;
+        }
         Workspace* ws = make_workspace(g, s->mem, !plain, sl.stream, &st);
         void* d_dist = ws ? s->mem->alloc((size_t)k * g->n * 4) : nullptr;
         if (!ws || !d_dist) {
             if (ws) free_workspace(g, ws);
             continue;  // does not fit now; another graph might, or wait for completions
         }
+        TraceRange tr("server_launch", k);
         Launch L;
         L.slot = free_slot;
         L.graph_id = (int32_t)gid;
@@ -141,22 +173,21 @@ static bool try_launch(bfs_server* s) {
             q.front()->launch_ns = t_launch;
             q.pop_front();
         }
-        // with other launches in flight, a share of the persistent grid so
-        // that they stay resident together; alone, the whole grid
         L.plain = plain;
-        const bool alone = s->inflight.empty();
+        L.cta = fp;
+        const int32_t full = plain ? plain_grid_of(g) : g->grid_batch;
+        const int32_t grid = alone ? full : s->ctx->sms;
+        L.ctas_per_sm = (grid + s->ctx->sms - 1) / s->ctx->sms;
         if (plain) {
-            const int32_t share =
-                alone ? plain_grid_of(g)
-                      : std::max<int32_t>(s->ctx->sms, plain_grid_of(g) / (int32_t)s->slots.size());
             for (int i = 0; i < k && st == BFS_OK; ++i)
                 st = run_plain_on(g, ws, roots[i], static_cast<int32_t*>(d_dist) + (size_t)i * g->n,
-                                  nullptr, sl.stream, 0, share);
+                                  nullptr, sl.stream, 0, grid);
         } else {
-            const int32_t share =
-                alone ? g->grid_batch
-                      : std::max<int32_t>(s->ctx->sms, g->grid_batch / (int32_t)s->slots.size());
-            st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, 0, share);
+            st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, 0, grid);
+        }
+        if (st == BFS_OK) {
+            cudaError_t e = cudaEventRecord(sl.kevent, sl.stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "event record");
         }
         if (st == BFS_OK) {
             for (int i = 0; i < k; ++i) {
@@ -289,15 +320,33 @@ bfs_status bfs_server_create(bfs_context* ctx, size_t memory_budget, int32_t num
         return BFS_ERR_NO_MEMORY;
     }
     s->mem = new DeviceAllocator(s->arena, memory_budget);
+    int regs = 0, threads = 0, smem = 0;
+    e = cudaDeviceGetAttribute(&regs, cudaDevAttrMaxRegistersPerMultiprocessor, ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&threads, cudaDevAttrMaxThreadsPerMultiProcessor, ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device);
+    if (e != cudaSuccess) {
+        bfs_status st = cuda_fail(e, "device attributes");
+        delete s->mem;
+        ctx->mem->release(s->arena);
+        delete s;
+        return st;
+    }
+    s->sm_regs = regs;
+    s->sm_threads = threads;
+    s->sm_smem = (size_t)smem;
     s->slots.resize((size_t)num_streams);
     for (auto& sl : s->slots) {
         e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.event, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.kevent, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             bfs_status st = cuda_fail(e, "stream creation");
             for (auto& x : s->slots) {
                 if (x.stream) cudaStreamDestroy(x.stream);
                 if (x.event) cudaEventDestroy(x.event);
+                if (x.kevent) cudaEventDestroy(x.kevent);
             }
             delete s->mem;
             ctx->mem->release(s->arena);
@@ -507,15 +556,19 @@ bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids
             set_error("replay: unknown graph or no buffers for it");
             return BFS_ERR_INVALID_ARG;
         }
-    // per-graph free buffers
+    // per-graph free buffers and query lists (arrival order within a graph)
     std::vector<std::vector<int>> free_slots(ng);
+    std::vector<std::vector<int64_t>> of_graph(ng);
     for (int g = 0; g < ng; ++g)
         for (int k = std::max(0, bufs_per_graph[g]) - 1; k >= 0; --k) free_slots[g].push_back(k);
+    for (int64_t i = 0; i < nq; ++i) of_graph[graph_ids[i]].push_back(i);
     std::vector<bfs_ticket> tickets((size_t)nq, 0);
     std::vector<int> slot_of((size_t)nq, 0);
+    std::vector<int64_t> fresh;  // submitted, not yet seen by the collector
     std::mutex mu;
     std::condition_variable cv;
     int64_t submitted = 0;
+    int submitters_left = 0;
     bfs_status first_err = BFS_OK;
     for (int64_t i = 0; i < nq; ++i) {
         done_ns[i] = 0;
@@ -526,15 +579,17 @@ bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids
     std::thread collector([&] {
         std::vector<int64_t> open, fin;
         std::vector<int64_t> opened_at;
-        int64_t taken = 0;
         for (;;) {
+            bool all_in = false;
             {
                 std::lock_guard<std::mutex> lk(mu);
-                while (taken < submitted) {
-                    open.push_back(taken++);
+                for (int64_t j : fresh) {
+                    open.push_back(j);
                     opened_at.push_back(now_ns());
                 }
-                if (open.empty() && (taken == nq || first_err != BFS_OK)) break;
+                fresh.clear();
+                all_in = submitters_left == 0;
+                if (open.empty() && all_in) break;
             }
             fin.clear();
             {
@@ -582,45 +637,101 @@ bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids
             }
         }
     });
-    for (int64_t i = 0; i < nq; ++i) {
-        const int g = graph_ids[i];
-        int slot = 0;
-        {
-            std::unique_lock<std::mutex> lk(mu);
-            auto any_free = [&] { return !free_slots[g].empty(); };
-            if (timeout_us < 0) cv.wait(lk, any_free);
-            else if (!cv.wait_for(lk, std::chrono::microseconds(timeout_us), any_free)) {
-                first_err = BFS_ERR_TIMEOUT;
+    // one submitter per graph: a graph whose buffers are all in use delays
+    // only its own later queries, as independent clients would
+    auto submit_graph = [&](int g) {
+        for (int64_t i : of_graph[g]) {
+            int slot = 0;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                if (first_err != BFS_OK) break;
+                auto any_free = [&] { return !free_slots[g].empty() || first_err != BFS_OK; };
+                if (timeout_us < 0) cv.wait(lk, any_free);
+                else if (!cv.wait_for(lk, std::chrono::microseconds(timeout_us), any_free)) {
+                    first_err = BFS_ERR_TIMEOUT;
+                    cv.notify_all();
+                    break;
+                }
+                if (first_err != BFS_OK) break;
+                slot = free_slots[g].back();
+                free_slots[g].pop_back();
+            }
+            for (;;) {  // until the arrival time
+                const int64_t now = now_ns();
+                if (now >= arrival_ns[i]) break;
+                if (arrival_ns[i] - now > 200000)
+                    std::this_thread::sleep_for(std::chrono::nanoseconds(arrival_ns[i] - now - 100000));
+            }
+            bfs_ticket t = 0;
+            const bfs_status st =
+                bfs_submit(s, g, roots[i], graph_bufs[g] + (size_t)slot * (size_t)ns[(size_t)g], &t);
+            std::lock_guard<std::mutex> lk(mu);
+            if (st != BFS_OK) {
+                first_err = st;
+                free_slots[g].push_back(slot);
                 cv.notify_all();
                 break;
             }
-            slot = free_slots[g].back();
-            free_slots[g].pop_back();
+            tickets[(size_t)i] = t;
+            slot_of[(size_t)i] = slot;
+            ++submitted;
+            fresh.push_back(i);
+            cv.notify_all();
         }
-        for (;;) {  // until the arrival time
+        std::lock_guard<std::mutex> lk(mu);
+        --submitters_left;
+        cv.notify_all();
+    };
+    std::vector<std::thread> submitters;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (int g = 0; g < ng; ++g)
+            if (!of_graph[g].empty()) ++submitters_left;
+    }
+    for (int g = 0; g < ng; ++g)
+        if (!of_graph[g].empty()) submitters.emplace_back(submit_graph, g);
+    for (auto& th : submitters) th.join();
+    collector.join();
+    if (first_err != BFS_OK) return first_err;
+    return BFS_OK;
+}
+
+bfs_status bfs_replay_single(bfs_graph* const* graphs, int32_t ngraphs, int64_t nq,
+                             const int32_t* graph_ids, const int32_t* roots,
+                             const int64_t* arrival_ns, int32_t* const* graph_bufs,
+                             const int32_t* bufs_per_graph, void* stream, int64_t* done_ns,
+                             int32_t* status_out) {
+    if (!graphs || ngraphs < 1 || nq < 0 ||
+        (nq > 0 && (!graph_ids || !roots || !arrival_ns || !graph_bufs || !bufs_per_graph ||
+                    !done_ns || !status_out))) {
+        set_error("null argument");
+        return BFS_ERR_INVALID_ARG;
+    }
+    for (int64_t i = 0; i < nq; ++i) {
+        const int g = graph_ids[i];
+        if (g < 0 || g >= ngraphs || !graphs[g] || bufs_per_graph[g] < 1 || !graph_bufs[g]) {
+            set_error("replay: unknown graph or no buffers for it");
+            return BFS_ERR_INVALID_ARG;
+        }
+    }
+    std::vector<int64_t> used((size_t)ngraphs, 0);
+    bfs_status first_err = BFS_OK;
+    for (int64_t i = 0; i < nq; ++i) {
+        const int g = graph_ids[i];
+        for (;;) {  // until the arrival time (queries run in arrival order)
             const int64_t now = now_ns();
             if (now >= arrival_ns[i]) break;
             if (arrival_ns[i] - now > 200000)
                 std::this_thread::sleep_for(std::chrono::nanoseconds(arrival_ns[i] - now - 100000));
         }
-        bfs_ticket t = 0;
-        const bfs_status st =
-            bfs_submit(s, g, roots[i], graph_bufs[g] + (size_t)slot * (size_t)ns[(size_t)g], &t);
-        std::lock_guard<std::mutex> lk(mu);
-        if (st != BFS_OK) {
-            first_err = st;
-            free_slots[g].push_back(slot);
-            cv.notify_all();
-            break;
-        }
-        tickets[(size_t)i] = t;
-        slot_of[(size_t)i] = slot;
-        ++submitted;
-        cv.notify_all();
+        int32_t* out = graph_bufs[g] + (size_t)(used[(size_t)g]++ % bufs_per_graph[g]) *
+                                           (size_t)graphs[g]->n;
+        const bfs_status st = bfs_run(graphs[g], roots[i], out, nullptr, stream, BFS_OUT_HOST);
+        done_ns[i] = now_ns();
+        status_out[i] = st;
+        if (st != BFS_OK && first_err == BFS_OK) first_err = st;
     }
-    collector.join();
-    if (first_err != BFS_OK) return first_err;
-    return BFS_OK;
+    return first_err;
 }
 
 bfs_status bfs_server_get_stats(bfs_server* s, bfs_server_stats* out) {
@@ -654,6 +765,7 @@ bfs_status bfs_server_destroy(bfs_server* s) {
         cudaStreamSynchronize(sl.stream);
         cudaStreamDestroy(sl.stream);
         cudaEventDestroy(sl.event);
+        cudaEventDestroy(sl.kevent);
     }
     delete s->mem;
     s->ctx->mem->release(s->arena);

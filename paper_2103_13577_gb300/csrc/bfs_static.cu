@@ -141,6 +141,7 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
         set_error("bfs_run_static: row_off must be 8-byte aligned");
         return BFS_ERR_INVALID_ARG;
     }
+    TraceRange tr("bfs_run_static", root);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: cudaGetDevice");

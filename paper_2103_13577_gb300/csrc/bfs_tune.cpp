@@ -102,6 +102,7 @@ using namespace bfs;
 extern "C" bfs_status bfs_graph_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots,
                                          uint32_t flags, const char* cache_path,
                                          bfs_tune_result* out) {
+    bfs::TraceRange tr("bfs_graph_autotune", nroots);
     if (!g || !roots || nroots < 1 || nroots > 64) {
         set_error("autotune: need a graph and 1..64 sample roots");
         return BFS_ERR_INVALID_ARG;

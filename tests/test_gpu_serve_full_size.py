@@ -43,8 +43,10 @@ def test_served_mix_every_row_equals_oracle():
                      dtype=np.int32)
     gaps = rng.exponential(1.0 / rate, nq)
     gaps[:nq // 2] = 0.0   # a burst first: queries queue behind busy slots and share launches
-    # one output row per query, so every result stays for the comparison
-    outs = [np.full(len(graphs[w][0]) - 1, -7, dtype=np.int32) for w in which]
+    # one pinned output row per query, so every result stays for the
+    # comparison and the server's result copies run asynchronously
+    outs = [torch.full((len(graphs[w][0]) - 1,), -7, dtype=torch.int32).pin_memory().numpy()
+            for w in which]
     tickets = []
     t0 = time.perf_counter()
     due = t0 + np.cumsum(gaps)
