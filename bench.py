@@ -160,7 +160,7 @@ def workload_config(n, m, world):
 
 def make_workload(rank):
     import graphgen
-    off, col = graphgen.kronecker(SCALE, EDGE_FACTOR, seed=GRAPH_SEED)
+    off, col, _ = workload_graph("kronecker", SCALE, EDGE_FACTOR, GRAPH_SEED)
     roots = graphgen.pick_roots(off, NROOTS, seed=ROOT_SEED + 7919 * rank)
     return off, col, roots
 
@@ -208,9 +208,11 @@ def paths_measure(bfs, torch, dev_, stream, off, col, roots, n):
     0-3 of uniform 0-7 (about half the entries); device time per root from
     CUDA events on the stream, scratch carved from an arena context.
     Algorithmic bytes per traversal: 4 m_c columns (+ 4 m_c weights when
-    filtered) + 56 n_c (row offsets 16, frontier queue 8, degree and scan
-    arrays 32) + 12 N (hops and sigma initialised); the random hops probes,
-    claims and sigma atomics are cache traffic."""
+    filtered) + 60 n_c (row offsets 16, frontier queue entry written and
+    read 24, sigma read as a frontier vertex 8 and written once 8, hops 4)
+    + 12 N (hops and sigma initialised); the visited-bitmap probes, the
+    next-frontier marks, the sigma additions and the per-level bitmap scans
+    (N / 8 bytes) are cache traffic, not counted."""
     peak, _ = measured_hbm_peak()
     arena = torch.empty(int(32 * n + (64 << 20)), dtype=torch.uint8, device=dev_)
     pctx = bfs.Context(dev_.index, arena=arena)
@@ -233,7 +235,7 @@ def paths_measure(bfs, torch, dev_, stream, off, col, roots, n):
             torch.cuda.synchronize(dev_)
             ms.append(ev[0].elapsed_time(ev[1]))
             edges.append(st["edges_scanned"])
-            nbytes.append((8 if w is not None else 4) * st["edges_scanned"] + 56 * st["reached"]
+            nbytes.append((8 if w is not None else 4) * st["edges_scanned"] + 60 * st["reached"]
                           + 12 * n)
         ms, edges, nbytes = np.array(ms), np.array(edges, dtype=np.float64), np.array(nbytes, dtype=np.float64)
         gbs = float(np.mean(nbytes / (ms * 1e-3)) / 1e9)
@@ -241,7 +243,7 @@ def paths_measure(bfs, torch, dev_, stream, off, col, roots, n):
                      "levels_last_root": int(st["levels"]),
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
                                   "frac": gbs / peak, "traffic": None,
-                                  "kernel": "paths_expand with paths_collect, paths_degrees and the scan",
+                                  "kernel": "paths_persistent",
                                   "algorithmic_bytes_per_traversal": float(nbytes.mean())}}
     pctx.close()
     del arena, d_off, d_col, d_w, hops, sigma
@@ -566,37 +568,59 @@ def gpu_arm(args, rank, world, local_rank):
             "clocks": clk,
             "gpu_launches": int(args.steps * NROOTS),
         }
-        print(json.dumps(line), flush=True)
     g.close()
     ctx.close()
+    if rank == 0:
+        if world == 1 and not args.no_extras:
+            # the other workloads, measured after the headline's timed region:
+            # 64-root batched at scale 24 and served queries at 1k / 10k q/s
+            del dist, parent
+            torch.cuda.empty_cache()
+            line["batched_s24"] = batched_measure(24)
+            line["serving"] = serve_measure([18, 20, 22, 24], [1000, 10000], 0.5, 10000, 32)
+        print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------- batched configuration
-def batched_arm(args):
+_GRAPHS = {}
+
+
+def workload_graph(kind, scale, k, seed):
+    """A seeded workload graph, generated once per process (the headline,
+    batched and serving workloads share graphs)."""
+    import graphgen
+    key = (kind, scale, k, seed)
+    if key not in _GRAPHS:
+        t0 = time.time()
+        gen = graphgen.kronecker if kind == "kronecker" else graphgen.erdos_renyi
+        off, col = gen(scale, k, seed=seed)
+        _GRAPHS[key] = (off, col, time.time() - t0)
+    return _GRAPHS[key]
+
+
+def batched_measure(scale):
     """64 roots in one launch vs 64 single-source runs, on a Kronecker graph
-    (scale 24, edge factor 16) and an Erdos-Renyi graph (2^24 vertices,
-    average degree 32), each autotuned first (plain and batched separately)."""
+    (edge factor 16) and an Erdos-Renyi graph (average degree 32) of 2^scale
+    vertices, each autotuned first (single-source on 4 roots, batched on all
+    64).  GTEPS = sum of the 64 roots' m_c / time."""
     import torch
 
     import graphgen
     import paper_2103_13577_gb300 as bfs
 
-    scale = args.batch_scale
-    out = {"metric": METRIC, "unit": "GTEPS", "workload": f"batched_64roots_s{scale}",
-           "higher_is_better": True, "data": "synthetic", "dtype": "int32", "graphs": []}
+    out = {"workload": f"batched_64roots_s{scale}", "unit": "GTEPS", "graphs": []}
     ctx = bfs.Context(0)
     stream = torch.cuda.current_stream()
-    for name, gen in (("kronecker", lambda: graphgen.kronecker(scale, 16, seed=24)),
-                      ("erdos_renyi", lambda: graphgen.erdos_renyi(scale, 32, seed=25))):
-        t0 = time.time()
-        off, col = gen()
-        gen_s = time.time() - t0
+    for name, spec in (("kronecker", ("kronecker", scale, 16, 24)),
+                       ("erdos_renyi", ("erdos_renyi", scale, 32, 25))):
+        off, col, gen_s = workload_graph(*spec)
         n = len(off) - 1
         roots = graphgen.pick_roots(off, NROOTS, seed=ROOT_SEED)
         g = bfs.Graph(ctx, off, col)
         dist = torch.empty(n, dtype=torch.int32, device="cuda")
         parent = torch.empty(n, dtype=torch.int32, device="cuda")
-        rec = {"graph": name, "vertices": n, "directed_entries": int(len(col)), "gen_s": gen_s}
+        rec = {"graph": name, "vertices": n, "directed_entries": int(len(col)), "gen_s": gen_s,
+               "seed": spec[3]}
         tune_plain = g.autotune(roots[:4])
         rec["tuned_plain"] = {k: tune_plain[k] for k in ("t_small", "t_large", "chunk_warp", "chunk_cta", "ctas_per_sm")}
 
@@ -656,111 +680,108 @@ def batched_arm(args):
         del dist, parent
         torch.cuda.empty_cache()
     ctx.close()
+    return out
+
+
+def batched_arm(args):
+    out = {"metric": METRIC, "higher_is_better": True, "data": "synthetic", "dtype": "int32"}
+    out.update(batched_measure(args.batch_scale))
     print(json.dumps(out), flush=True)
 
 
 # --------------------------------------------------- serving configuration
-def serve_arm(args):
-    """Served single-root queries on four resident Kronecker graphs (scales
-    18, 20, 22, 24, edge factor 16): seeded Poisson arrivals at each offered
-    rate, graph uniform, root uniform among degree >= 1 vertices; the server
-    packs same-graph queries into batched launches on 4 streams within a
-    fixed memory budget.  Latency = completion on the server's monotonic
-    clock minus the scheduled arrival; the result copy to the caller's pinned
-    host buffer is inside it.  Baseline: the same arrivals served one at a
-    time by bfs_run (FIFO, arrival order), from measured per-graph service
-    times.  The trace is replayed by bfs_server_replay (native submitter and
-    collector threads)."""
+def serve_measure(scales, rates, window_s, max_queries, budget_gib, buf_gib=8.0):
+    """Served single-root queries on resident Kronecker graphs (edge factor
+    16, graph seed = scale; the scale-22 and scale-24 graphs are the headline
+    and batched workloads' graphs): seeded Poisson arrivals at each offered
+    rate, graph uniform, root uniform over a seeded pool of 256 degree >= 1
+    vertices per graph; the server packs same-graph queries into batched
+    launches on 4 streams within a fixed memory budget.  The trace is
+    replayed by bfs_server_replay (one native submitter thread per graph, a
+    native collector).  Latency = completion on the server's monotonic clock
+    minus the scheduled arrival; the copy of the result row into the
+    caller's pinned host buffer is inside it.  Baseline: the same trace run
+    one query at a time by bfs_replay_single (bfs_run with a host row, in
+    arrival order, from a native thread), measured, not modelled."""
     import torch
 
     import graphgen
     import paper_2103_13577_gb300 as bfs
 
-    scales = [int(x) for x in args.serve_scales.split(",")]
     ctx = bfs.Context(0)
     graphs = []
     for sc in scales:
-        off, col = graphgen.kronecker(sc, 16, seed=100 + sc)
+        off, col, _ = workload_graph("kronecker", sc, 16, sc)
         g = bfs.Graph(ctx, off, col)
         g.set_option(bfs.BFS_OPT_DIRECTION, 1)
         pool_roots = graphgen.pick_roots(off, 256, seed=200 + sc)
-        graphs.append({"scale": sc, "n": len(off) - 1, "g": g, "roots": pool_roots,
-                       "off": off, "col": col})
-    srv = bfs.Server(ctx, args.serve_budget << 30, num_streams=4)
+        graphs.append({"scale": sc, "n": len(off) - 1, "g": g, "roots": pool_roots})
+    srv = bfs.Server(ctx, int(budget_gib) << 30, num_streams=4)
     for gr in graphs:
         gr["gid"] = srv.add_graph(gr["g"])
-        nbuf = int(max(8, min(256, (2 << 30) // (gr["n"] * 4))))
+        nbuf = int(max(8, min(256, int(buf_gib * (1 << 30)) // (gr["n"] * 4))))
         gr["bufs"] = torch.empty((nbuf, gr["n"]), dtype=torch.int32, pin_memory=True).numpy()
-
-    # baseline service times: bfs_run with a pinned host output, per graph
-    svc = []
-    for gr in graphs:
-        h = torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy()
-        for r in gr["roots"][:3]:
-            gr["g"].run(int(r), h)
-        ts = []
-        for r in gr["roots"][3:19]:
-            t0 = time.perf_counter()
-            gr["g"].run(int(r), h)
-            ts.append(time.perf_counter() - t0)
-        svc.append(float(np.mean(ts)))
-
+        gr["base_bufs"] = gr["bufs"][:2]
+    handles = [gr["g"].handle for gr in graphs]
     results = []
-    for rate in [int(x) for x in args.serve_rates.split(",")]:
-        nq = int(min(args.serve_max_queries, rate * args.serve_window))
+    for rate in rates:
+        nq = int(min(max_queries, rate * window_s))
         rng = np.random.default_rng(rate)
         gaps = rng.exponential(1.0 / rate, nq)
         which = rng.integers(0, len(graphs), nq)
         ridx = rng.integers(0, 256, nq)
-        t0 = time.monotonic_ns() + 20_000_000
-        arrival = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
-        # the trace is submitted and collected by the library's native replay
-        # threads (no Python in the loop); a query takes any free pinned buffer
-        # of its graph and waits for one when all are in use
         gid = np.array([graphs[w]["gid"] for w in which], dtype=np.int32)
         rts = np.array([graphs[w]["roots"][j] for w, j in zip(which, ridx)], dtype=np.int32)
+        st0 = srv.stats()
+        t0 = time.monotonic_ns() + 20_000_000
+        arrival = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
         done, status, _ = srv.replay(gid, rts, arrival, [gr["bufs"] for gr in graphs],
-                                     timeout_us=60_000_000)
-        errors = [int(x) for x in status if x != bfs.BFS_OK]
+                                     timeout_us=120_000_000)
+        st1 = srv.stats()
+        errors = int(np.count_nonzero(status != bfs.BFS_OK))
         lat_ms = (done - arrival) / 1e6
         span_s = (done.max() - arrival[0]) / 1e9
-        # FIFO model of the same arrivals served one query at a time
-        end = 0.0
-        base_lat = np.empty(nq)
-        arr_s = (arrival - arrival[0]) / 1e9
-        for i in range(nq):
-            start = max(arr_s[i], end)
-            end = start + svc[which[i]]
-            base_lat[i] = (end - arr_s[i]) * 1e3
+        # the same trace, one query at a time
+        t0 = time.monotonic_ns() + 20_000_000
+        arrival_b = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
+        done_b, status_b = bfs.bfs_replay_single(handles, which.astype(np.int32), rts, arrival_b,
+                                                 [gr["base_bufs"] for gr in graphs])
+        lat_b = (done_b - arrival_b) / 1e6
+        launches = st1["launches"] - st0["launches"]
         results.append({
-            "offered_qps": rate, "queries": nq, "errors": len(errors),
+            "offered_qps": rate, "queries": nq, "errors": errors,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "sustained_qps": nq / span_s,
-            "plain_fifo_p50_ms": float(np.percentile(base_lat, 50)),
-            "plain_fifo_p99_ms": float(np.percentile(base_lat, 99)),
-            "plain_fifo_qps": nq / (end if end > 0 else 1.0),
+            "launches": int(launches),
+            "mean_queries_per_launch": (st1["lanes"] - st0["lanes"]) / max(1, launches),
+            "one_at_a_time": {
+                "p50_ms": float(np.percentile(lat_b, 50)),
+                "p99_ms": float(np.percentile(lat_b, 99)),
+                "sustained_qps": nq / ((done_b.max() - arrival_b[0]) / 1e9),
+                "errors": int(np.count_nonzero(status_b != bfs.BFS_OK))},
         })
-    st = srv.stats()
-    # spot-check a few served results against single-source runs
-    check_ok = True
-    for gr in graphs:
-        h = torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy()
-        ref = torch.empty(gr["n"], dtype=torch.int32, pin_memory=True).numpy()
-        r = int(gr["roots"][0])
-        t = srv.submit(gr["gid"], r, h)
-        srv.wait(t, 60_000_000)
-        srv.release(t)
-        gr["g"].run(r, ref)
-        check_ok = check_ok and bool(np.array_equal(h, ref))
     srv.close()
-    out = {"metric": METRIC, "workload": "served_queries_kronecker_s" + "_".join(map(str, scales)),
-           "unit": "ms", "data": "synthetic", "memory_budget_gib": args.serve_budget,
-           "streams": 4, "window_s": args.serve_window, "rates": results,
-           "plain_service_ms": {f"s{gr['scale']}": t * 1e3 for gr, t in zip(graphs, svc)},
-           "server": st, "served_equals_single_source": check_ok}
+    out = {"workload": "served_queries_kronecker_s" + "_".join(map(str, scales)), "unit": "ms",
+           "memory_budget_gib": budget_gib, "streams": 4, "window_s": window_s,
+           "host_buffers_per_graph": {f"s{gr['scale']}": int(gr["bufs"].shape[0]) for gr in graphs},
+           "rates": results, "server": srv_stats_of(st1),
+           "baseline": "the same arrival trace through bfs_replay_single: bfs_run with a pinned "
+                       "host row per query, in arrival order (measured)"}
     for gr in graphs:
         gr["g"].close()
     ctx.close()
+    return out
+
+
+def srv_stats_of(st):
+    return {k: int(v) for k, v in st.items()}
+
+
+def serve_arm(args):
+    out = {"metric": METRIC, "data": "synthetic"}
+    out.update(serve_measure([int(x) for x in args.serve_scales.split(",")],
+                             [int(x) for x in args.serve_rates.split(",")], args.serve_window,
+                             args.serve_max_queries, args.serve_budget))
     print(json.dumps(out), flush=True)
 
 
@@ -963,6 +984,8 @@ def main():
     ap.add_argument("--bins", default="", help="t_small,t_large,chunk_warp,chunk_cta")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="headline line only: skip the scale-24 batched and serving sections")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--serve-scales", default="18,20,22,24")
     ap.add_argument("--serve-rates", default="1000,10000,50000")

@@ -580,22 +580,29 @@ __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<fa
 // not seen yet into next[u].  visited only changes in phase B, so a cached
 // value is a safe filter; next[u] is read first so that lanes already
 // present skip the atomic (a fire-and-forget red.or otherwise).
+// The K pairs are read in groups of kBatchProbeGroup (4 at 3 CTAs/SM: 8
+// would keep 32 registers of pairs live, which spills at that occupancy).
 template <int K>
 __device__ __forceinline__ void visit_batch_k(const TraversalParams& P, unsigned okm,
                                               const int32_t (&u)[K],
                                               const uint64_t (&mask)[K]) {
-    // visited and next of a vertex are adjacent: one 16-byte load each
-    ulonglong2 vn[K];
+    constexpr int G = K < 4 ? K : 4;
 #pragma unroll
-    for (int j = 0; j < K; ++j)
-        vn[j] = ((okm >> j) & 1u) ? *reinterpret_cast<const ulonglong2*>(P.lane_vn + 2 * (long long)u[j])
-                                  : make_ulonglong2(~0ull, ~0ull);
+    for (int j0 = 0; j0 < K; j0 += G) {
+        // visited and next of a vertex are adjacent: one 16-byte load each
+        ulonglong2 vn[G];
 #pragma unroll
-    for (int j = 0; j < K; ++j) {
-        const uint64_t m = mask[j] & ~vn[j].x;
-        if ((m & ~vn[j].y) != 0ull)
-            atomicOr(reinterpret_cast<unsigned long long*>(P.lane_vn + 2 * (long long)u[j] + 1),
-                     (unsigned long long)m);
+        for (int j = 0; j < G; ++j)
+            vn[j] = ((okm >> (j0 + j)) & 1u)
+                        ? *reinterpret_cast<const ulonglong2*>(P.lane_vn + 2 * (long long)u[j0 + j])
+                        : make_ulonglong2(~0ull, ~0ull);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const uint64_t m = mask[j0 + j] & ~vn[j].x;
+            if ((m & ~vn[j].y) != 0ull)
+                atomicOr(reinterpret_cast<unsigned long long*>(P.lane_vn + 2 * (long long)u[j0 + j] + 1),
+                         (unsigned long long)m);
+        }
     }
 }
 
@@ -793,6 +800,87 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
     }
 }
 
+// Valid columns of the 16-byte unit holding row-relative columns [r, r + 4)
+// of a row whose valid columns are [lo, hi): bits [lo - r, hi - r) of 4.
+__device__ __forceinline__ unsigned unit_mask(int r, int lo, int hi) {
+    const int a = min(max(lo - r, 0), 4), b = min(max(hi - r, 0), 4);
+    return ((1u << b) - 1u) & ~((1u << a) - 1u);
+}
+
+// Column units through shared memory (BFS_ASYNC_COLS): round r + 1's units
+// are copied by cp.async (16 bytes per unit, L1 bypassed) into the warp's
+// second buffer while round r's are probed, so a round's column loads no
+// longer sit on its critical path and no registers hold them in flight.
+// Each lane reads back only the units it copied, so no warp barrier is
+// needed between the copies and the reads.  units: the warp's rows cut into
+// 16-byte units laid end to end (excl = exclusive prefix per lane, total =
+// all units); a4/rlo/rhi/v: the lane's row start (16-byte aligned), its
+// valid columns and vertex.
+#ifndef BFS_ASYNC_COLS
+#define BFS_ASYNC_COLS 0
+#endif
+constexpr bool kAsyncCols = BFS_ASYNC_COLS != 0;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_one() {  // all but the newest group done
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+__device__ __forceinline__ void expand_units_async(const TraversalParams& P, Stage<false>& S,
+                                                   int total, int excl, long long a4, int rlo,
+                                                   int rhi, int32_t v, int level, int nxt,
+                                                   int nslot) {
+    __shared__ __align__(16) int4 s_units[kWarps][2][64];
+    const unsigned lane = lane_id();
+    int4 (*buf)[64] = s_units[threadIdx.x >> 5];
+    unsigned okm_n = 0u;
+    int32_t vo_n[2] = {0, 0};
+    // copy round q0's units into buffer b, keep their masks and vertices
+    auto issue = [&](int q0, int b) {
+        okm_n = 0u;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int q = q0 + 32 * h + (int)lane;
+            int o = 0;
+#pragma unroll
+            for (int st = 16; st > 0; st >>= 1) {
+                const int c = o + st;
+                if (__shfl_sync(FULL_MASK, excl, c & 31) <= q) o = c;
+            }
+            const long long a4o = __shfl_sync(FULL_MASK, a4, o);
+            const int lo_o = __shfl_sync(FULL_MASK, rlo, o);
+            const int hi_o = __shfl_sync(FULL_MASK, rhi, o);
+            const int xo = __shfl_sync(FULL_MASK, excl, o);
+            vo_n[h] = __shfl_sync(FULL_MASK, v, o);
+            if (q < total) {
+                const int r = 4 * (q - xo);
+                cp_async16(&buf[b][32 * h + lane], P.col + a4o + r);
+                okm_n |= unit_mask(r, lo_o, hi_o) << (4 * h);
+            }
+        }
+        cp_async_commit();
+    };
+    if (total > 0) issue(0, 0);
+    int b = 0;
+    for (int q0 = 0; q0 < total; q0 += 64, b ^= 1) {
+        const unsigned okm = okm_n;
+        const int32_t v0 = vo_n[0], v1 = vo_n[1];
+        if (q0 + 64 < total) issue(q0 + 64, b ^ 1);
+        else cp_async_commit();  // an empty group keeps "all but the newest" meaning this round
+        cp_async_wait_one();
+        const int4 x0 = buf[b][lane], x1 = buf[b][32 + lane];
+        const int32_t u[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        const int32_t vv[8] = {v0, v0, v0, v0, v1, v1, v1, v1};
+        visit_plain_k<8>(P, S, okm, u, vv, level, nxt, nslot);
+    }
+}
+
 // Bin 1: one warp per chunk of chunk_warp edges.  The chunk's vertex
 // segments (up to 32 at a time) are cut into 16-byte units (4 columns, the
 // first rounded down to a 16-byte boundary) laid end to end by a scan; each
@@ -832,6 +920,12 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
         const int incl = warp_incl_scan(units);
         const int excl = incl - units;
         const int total = __shfl_sync(FULL_MASK, incl, 31);
+        if constexpr (!kBatch && kAsyncCols) {
+            expand_units_async(P, S, total, excl, a4, rlo, rhi, v, level, nxt, nslot);
+            if (__popc(okb) < 32) break;
+            i += 32;
+            continue;
+        }
         for (int q0 = 0; q0 < total; q0 += 64) {
             unsigned okm = 0u;
             int32_t u[8], vv[8];
@@ -855,9 +949,7 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
                 int4 x = make_int4(0, 0, 0, 0);
                 if (q < total) {
                     x = __ldcs(reinterpret_cast<const int4*>(P.col + a4o + r));
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (r + c >= lo_o && r + c < hi_o) okm |= 1u << (4 * h + c);
+                    okm |= unit_mask(r, lo_o, hi_o) << (4 * h);
                 }
                 u[4 * h + 0] = x.x;
                 u[4 * h + 1] = x.y;
@@ -1155,6 +1247,10 @@ __device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, lo
         const int incl = warp_incl_scan(units);
         const int excl = incl - units;
         const int total = __shfl_sync(FULL_MASK, incl, 31);
+        if constexpr (kAsyncCols) {
+            expand_units_async(P, S, total, excl, a4, rlo, rhi, v, level, nxt, nslot);
+            continue;
+        }
         for (int q0 = 0; q0 < total; q0 += 64) {
             unsigned okm = 0u;
             int32_t u[8], vv[8];
@@ -1177,9 +1273,7 @@ __device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, lo
                 int4 x = make_int4(0, 0, 0, 0);
                 if (q < total) {
                     x = __ldcs(reinterpret_cast<const int4*>(P.col + a4o + r));
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (r + c >= lo_o && r + c < hi_o) okm |= 1u << (4 * h + c);
+                    okm |= unit_mask(r, lo_o, hi_o) << (4 * h);
                 }
                 u[4 * h + 0] = x.x;
                 u[4 * h + 1] = x.y;
@@ -1653,57 +1747,72 @@ __device__ void sweep_batch(const TraversalParams& P, Stage<true>& S, int level,
     long long my_pairs = 0, my_full = 0;
     unsigned long long my_front = 0ull;  // lanes with a vertex in the next frontier
     const uint64_t all_lanes = P.nlanes >= 64 ? ~0ull : ((1ull << P.nlanes) - 1ull);
-    const long long nround = (P.n + 31) / 32 * 32;  // warp-uniform trip count
-    for (long long v = tid; v < nround; v += nthreads) {
-        uint64_t fresh = 0ull;
-        bool reached_before = false;  // some lane had reached v at an earlier level
-        if (v < P.n) {
-            ulonglong2* const pv = reinterpret_cast<ulonglong2*>(P.lane_vn) + v;
-            const ulonglong2 vn = __ldcg(pv);
-            if (vn.y != 0ull) {
-                fresh = vn.y & ~vn.x;
-                reached_before = vn.x != 0ull;
-                *pv = make_ulonglong2(vn.x | fresh, 0ull);
-                my_pairs += __popcll(fresh);
-                // bottom-up bookkeeping: edges of vertices every lane has now reached
-                if (P.dir_mode != 0 && fresh != 0ull && (vn.x | fresh) == all_lanes)
-                    my_full += __ldg(P.off + v + 1) - __ldg(P.off + v);
-            }
-            if (P.dir_mode != 0) P.lane_front[v] = fresh;
-            my_front |= fresh;
+    // kSweepUnroll vertices per thread and pass, their lane-set pairs loaded
+    // together; the trip count is the same for every thread (the stage push
+    // is warp-collective)
+    constexpr int kSweepUnroll = 4;
+    const long long stride = nthreads * kSweepUnroll;
+    const long long nround = (P.n + stride - 1) / stride * stride;
+    ulonglong2* const pairs = reinterpret_cast<ulonglong2*>(P.lane_vn);
+    for (long long v0 = tid; v0 < nround; v0 += stride) {
+        ulonglong2 vnu[kSweepUnroll];
+#pragma unroll
+        for (int x = 0; x < kSweepUnroll; ++x) {
+            const long long v = v0 + x * nthreads;
+            vnu[x] = v < P.n ? __ldcg(pairs + v) : make_ulonglong2(0ull, 0ull);
         }
-        // levels: one read-modify-write of the vertex's 64-byte level row
-        // (16-byte accesses, consecutive vertices' rows adjacent), bytes of
-        // the new lanes set to level + 1; bytes of lanes not reached yet are
-        // never read, so a first visit skips the read
-        if (fresh != 0ull) {
-            uint4* row = reinterpret_cast<uint4*>(P.lane_level + v * 64);
-            uint4 q[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                q[k] = reached_before ? __ldcg(row + k) : make_uint4(0, 0, 0, 0);
-            const int lvl = level + 1 < 255 ? level + 1 : 255;
-            const unsigned long long lvl8 = (unsigned long long)lvl * 0x0101010101010101ull;
-            unsigned long long* w = reinterpret_cast<unsigned long long*>(q);
-#pragma unroll
-            for (int g = 0; g < 8; ++g) {
-                const unsigned long long bm = byte_mask_of_bits((unsigned)(fresh >> (8 * g)) & 0xffu);
-                w[g] = (w[g] & ~bm) | (lvl8 & bm);
+        for (int x = 0; x < kSweepUnroll; ++x) {
+            const long long v = v0 + x * nthreads;
+            uint64_t fresh = 0ull;
+            bool reached_before = false;  // some lane had reached v at an earlier level
+            if (v < P.n) {
+                const ulonglong2 vn = vnu[x];
+                if (vn.y != 0ull) {
+                    fresh = vn.y & ~vn.x;
+                    reached_before = vn.x != 0ull;
+                    pairs[v] = make_ulonglong2(vn.x | fresh, 0ull);
+                    my_pairs += __popcll(fresh);
+                    // bottom-up bookkeeping: edges of vertices every lane has now reached
+                    if (P.dir_mode != 0 && fresh != 0ull && (vn.x | fresh) == all_lanes)
+                        my_full += __ldg(P.off + v + 1) - __ldg(P.off + v);
+                }
+                if (P.dir_mode != 0) P.lane_front[v] = fresh;
+                my_front |= fresh;
             }
-#pragma unroll
-            for (int k = 0; k < 4; ++k) row[k] = q[k];
-            if (level + 1 >= 255) {
-                // deep levels: the distance goes straight to the output
-                const int32_t cv = P.new2old ? __ldg(P.new2old + v) : (int32_t)v;
-                for (unsigned long long f = fresh; f != 0ull; f &= f - 1ull) {
-                    const long long idx = (long long)(__ffsll((long long)f) - 1) * P.n + cv;
-                    if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)(level + 1);
-                    else P.dist[idx] = level + 1;
+            // levels: one read-modify-write of the vertex's 64-byte level row
+            // (16-byte accesses, consecutive vertices' rows adjacent), bytes of
+            // the new lanes set to level + 1; bytes of lanes not reached yet are
+            // never read, so a first visit skips the read
+            if (fresh != 0ull) {
+                uint4* row = reinterpret_cast<uint4*>(P.lane_level + v * 64);
+                uint4 q[4];
+    #pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    q[k] = reached_before ? __ldcg(row + k) : make_uint4(0, 0, 0, 0);
+                const int lvl = level + 1 < 255 ? level + 1 : 255;
+                const unsigned long long lvl8 = (unsigned long long)lvl * 0x0101010101010101ull;
+                unsigned long long* w = reinterpret_cast<unsigned long long*>(q);
+    #pragma unroll
+                for (int g = 0; g < 8; ++g) {
+                    const unsigned long long bm = byte_mask_of_bits((unsigned)(fresh >> (8 * g)) & 0xffu);
+                    w[g] = (w[g] & ~bm) | (lvl8 & bm);
+                }
+    #pragma unroll
+                for (int k = 0; k < 4; ++k) row[k] = q[k];
+                if (level + 1 >= 255) {
+                    // deep levels: the distance goes straight to the output
+                    const int32_t cv = P.new2old ? __ldg(P.new2old + v) : (int32_t)v;
+                    for (unsigned long long f = fresh; f != 0ull; f &= f - 1ull) {
+                        const long long idx = (long long)(__ffsll((long long)f) - 1) * P.n + cv;
+                        if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)(level + 1);
+                        else P.dist[idx] = level + 1;
+                    }
                 }
             }
+            stage_push<true>(P, S, fresh != 0ull, (int32_t)(v < P.n ? v : 0), 0, fresh, level, nxt,
+                             nslot);
         }
-        stage_push<true>(P, S, fresh != 0ull, (int32_t)(v < P.n ? v : 0), 0, fresh, level, nxt,
-                         nslot);
     }
     stage_flush<true>(P, S, level, nxt, nslot);
     if (P.dir_mode != 0) {
@@ -1903,8 +2012,8 @@ __global__ void degree_bins_kernel(const int64_t* off, long long n, int t_small,
 
 // -------------------------------------------------------- host wrappers
 // Kernels are instantiated for 2, 3 and 4 resident CTAs per SM (register
-// cap 128, 80 or 64; batched kernels 2 and 3); the graph's occupancy option
-// picks one.
+// cap 128, 80 or 64; batched kernels 2 and 3: at 4 their spills cost more
+// than the extra warps gain); the graph's occupancy option picks one.
 const void* plain_persistent_fn(int mb, bool staged) {
     if (staged)
         return mb >= 4 ? (const void*)bfs_plain_persistent<4, true>
