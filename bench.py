@@ -46,6 +46,8 @@ WORKLOAD = "kronecker_s22_ef16_plain_64roots"
 KERNEL_SRC = os.path.join(ROOT, "paper_2103_13577_gb300", "csrc", "bfs_kernels.cu")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_plain_persistent_kron_s22_traffic.json")
 BATCH_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "bfs_batch_persistent_kron_s22_traffic.json")
+PATHS_SRC = os.path.join(ROOT, "paper_2103_13577_gb300", "csrc", "bfs_paths.cu")
+PATHS_TRAFFIC_FILE = os.path.join(ROOT, "profiles", "paths_persistent_kron_s22_traffic.json")
 
 
 def env_int(name, default):
@@ -75,18 +77,18 @@ def measured_hbm_peak():
         return 6800.0, "fallback"
 
 
-def kernel_hash():
-    with open(KERNEL_SRC, "rb") as f:
+def kernel_hash(src=KERNEL_SRC):
+    with open(src, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic(path=TRAFFIC_FILE):
+def recorded_traffic(path=TRAFFIC_FILE, src=KERNEL_SRC):
     """DRAM bytes per launch from the committed ncu capture, or None when the
     kernel source changed since the capture."""
     try:
         with open(path) as f:
             rec = json.load(f)
-        if rec.get("kernel_sha256_16") != kernel_hash():
+        if rec.get("kernel_sha256_16") != kernel_hash(src):
             return None
         return float(rec["dram_bytes_per_launch"])
     except Exception:
@@ -242,7 +244,9 @@ def paths_measure(bfs, torch, dev_, stream, off, col, roots, n):
         out[name] = {"gteps": hmean(edges / (ms * 1e-3) / 1e9), "root_ms_median": float(np.median(ms)),
                      "levels_last_root": int(st["levels"]),
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
-                                  "frac": gbs / peak, "traffic": None,
+                                  "frac": gbs / peak,
+                                  "traffic": recorded_traffic(PATHS_TRAFFIC_FILE, PATHS_SRC)
+                                  if name == "all_entries" else None,
                                   "kernel": "paths_persistent",
                                   "algorithmic_bytes_per_traversal": float(nbytes.mean())}}
     pctx.close()

@@ -263,11 +263,11 @@ bfs_status bfs_batch_sync(bfs_graph* g, void* stream, bfs_run_stats* stats);
  * graph's own options, e.g. BFS_OPT_DIRECTION).  Launches run on num_streams CUDA
  * streams so work from different graphs overlaps on the device.  A launch is
  * admitted only while the device memory of all launches in flight stays
- * within memory_budget bytes, and, next to launches whose kernels are still
- * running, only while one CTA of each fits on one SM together (each such
- * launch then runs one CTA per SM; a launch made while nothing else runs
- * gets the whole grid): every persistent grid is then resident at once and
- * none waits on another's SMs.  Queries that do not fit wait.  A query whose
+ * within memory_budget bytes; it takes as many CTAs per SM as fit next to
+ * the CTAs of the launches whose kernels are still running (registers,
+ * threads, shared memory; the whole grid when nothing else runs), and waits
+ * when not even one fits: every persistent grid is then resident at once
+ * and none waits on another's SMs.  Queries that do not fit wait.  A query whose
  * smallest launch alone exceeds the budget fails with BFS_ERR_BUDGET.
  * dist_out (host, int32[n]) is written when the query completes; the pointer
  * must stay valid until then.  Give pinned memory (cudaHostAlloc or a pinned

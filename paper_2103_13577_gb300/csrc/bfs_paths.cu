@@ -166,12 +166,12 @@ __device__ __forceinline__ void mark_tiles(const PathParams& P, int nxt, long lo
 __device__ void expand_paths(const PathParams& P, int cur, long long cnt, long long E) {
     __shared__ int32_t s_rel[kPathWarps][kPathTile + 1];   // first tile entry of each span entry
     __shared__ long long s_k[kPathWarps][kPathTile + 1];    // row shift
-    __shared__ int32_t s_v[kPathWarps][kPathTile + 1];
+    __shared__ double s_sig[kPathWarps][kPathTile + 1];     // sigma of the row's vertex (final)
     const unsigned lane = threadIdx.x & 31u;
     const int w = threadIdx.x >> 5;
     int32_t* const rel = s_rel[w];
     long long* const ks = s_k[w];
-    int32_t* const vs = s_v[w];
+    double* const sg = s_sig[w];
     const int32_t* qv = P.qv[cur];
     const int64_t* qe = P.qe[cur];
     const int64_t* qk = P.qk[cur];
@@ -197,11 +197,11 @@ __device__ void expand_paths(const PathParams& P, int cur, long long cnt, long l
             const long long eo = __ldcg(qe + first + i);
             rel[i] = (int32_t)max(eo - t0, 0ll);
             ks[i] = __ldcg(qk + first + i);
-            vs[i] = __ldcg(qv + first + i);
+            sg[i] = __ldcg(P.sigma + __ldcg(qv + first + i));
         }
         __syncwarp();
         int32_t u[kPathPerLane];
-        int32_t v[kPathPerLane];
+        double sv[kPathPerLane];
         bool take[kPathPerLane];
         int o = 0;
 #pragma unroll
@@ -209,7 +209,7 @@ __device__ void expand_paths(const PathParams& P, int cur, long long cnt, long l
             const int r = j * 32 + (int)lane;   // tile entry
             take[j] = false;
             u[j] = 0;
-            v[j] = 0;
+            sv[j] = 0.0;
             if (r < len) {
                 // rows are in order: search from the previous entry's row
                 if (o + 1 < span && rel[o + 1] <= r) {
@@ -222,7 +222,7 @@ __device__ void expand_paths(const PathParams& P, int cur, long long cnt, long l
                     o = a;
                 }
                 const long long k = t0 + r + ks[o];
-                v[j] = vs[o];
+                sv[j] = sg[o];
                 u[j] = __ldcs(P.col + k);
                 if (P.weight) {
                     const int32_t wt = __ldcs(P.weight + k);
@@ -232,6 +232,10 @@ __device__ void expand_paths(const PathParams& P, int cur, long long cnt, long l
                 }
             }
         }
+        // visited probes: a plain (L1-cacheable) read first -- an L1 copy
+        // from an earlier level can only show clear a bit that is set since,
+        // never the reverse -- and a read through L2 for the bits it shows
+        // clear, which decides
         uint32_t wd[kPathPerLane];
 #pragma unroll
         for (int j = 0; j < kPathPerLane; ++j) {
@@ -239,13 +243,16 @@ __device__ void expand_paths(const PathParams& P, int cur, long long cnt, long l
                 P.ctl->bad = 1;
                 take[j] = false;
             }
-            wd[j] = take[j] ? __ldcg(P.vis + (u[j] >> 5)) : 0xffffffffu;
+            wd[j] = take[j] ? P.vis[u[j] >> 5] : 0xffffffffu;
         }
+#pragma unroll
+        for (int j = 0; j < kPathPerLane; ++j)
+            if (!((wd[j] >> (u[j] & 31)) & 1u)) wd[j] = __ldcg(P.vis + (u[j] >> 5));
 #pragma unroll
         for (int j = 0; j < kPathPerLane; ++j) {
             if (take[j] && !((wd[j] >> (u[j] & 31)) & 1u)) {
                 atomicOr(P.mark + (u[j] >> 5), 1u << (u[j] & 31));
-                atomicAdd(P.sigma + u[j], __ldcg(P.sigma + v[j]));
+                atomicAdd(P.sigma + u[j], sv[j]);
             }
         }
         __syncwarp();

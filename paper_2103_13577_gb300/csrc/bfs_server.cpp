@@ -12,10 +12,10 @@
 // records an event.  Completed events release the memory, which admits
 // the next launch -- so queries that arrive while others are on the GPU
 // join the next launch on a free slot, and launches on different slots
-// overlap on the device: a launch made while others are in flight gets one
-// CTA per SM and is admitted only while the CTAs of all launches in flight
-// fit one SM side by side (registers, threads, shared memory), so every
-// persistent grid is resident at once and none waits on another's SMs.
+// overlap on the device: a launch takes as many CTAs per SM as fit next to
+// the CTAs of the launches whose kernels are still running (registers,
+// threads, shared memory), so every persistent grid is resident at once
+// and none waits on another's SMs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -132,27 +132,30 @@ static bool try_launch(bfs_server* s) {
         bfs_status st = BFS_OK;
         cudaSetDevice(s->ctx->device);
         // A cooperative launch is only guaranteed to be resident by itself.
-        // Alone it takes the whole grid; next to others it takes one CTA per
-        // SM, and only while every launch in flight fits one SM together
-        // (two launches that each got part of their grid would wait on each
-        // other's SMs at their grid barriers).
+        // Each launch takes as many CTAs per SM as fit next to the CTAs of
+        // the launches whose kernels are still running (up to its own full
+        // grid), so every persistent grid is resident at once: two launches
+        // that each got part of their grid would wait on each other's SMs at
+        // their grid barriers.  None fits: wait for a kernel to finish.
         CtaFootprint fp;
         if (cta_footprint(g, !plain, &fp) != BFS_OK) continue;
-        const bool alone = s->inflight.empty();
-        if (!alone) {
-            long long regs = fp.regs, threads = fp.threads;
-            size_t smem = fp.smem;
-            for (const Launch& o : s->inflight) {
-                // a launch whose kernels are done holds no SM resources while
-                // its result copies run
-                if (cudaEventQuery(s->slots[o.slot].kevent) == cudaSuccess) continue;
-                cudaGetLastError();
-                regs += (long long)o.ctas_per_sm * o.cta.regs;
-                threads += (long long)o.ctas_per_sm * o.cta.threads;
-                smem += (size_t)o.ctas_per_sm * o.cta.smem;
-            }
-            if (regs > s->sm_regs || threads > s->sm_threads || smem > s->sm_smem) continue;
+        long long regs = 0, threads = 0;
+        size_t smem = 0;
+        for (const Launch& o : s->inflight) {
+            // a launch whose kernels are done holds no SM resources while
+            // its result copies run
+            if (cudaEventQuery(s->slots[o.slot].kevent) == cudaSuccess) continue;
+            cudaGetLastError();
+            regs += (long long)o.ctas_per_sm * o.cta.regs;
+            threads += (long long)o.ctas_per_sm * o.cta.threads;
+            smem += (size_t)o.ctas_per_sm * o.cta.smem;
         }
+        const int32_t full = plain ? plain_grid_of(g) : g->grid_batch;
+        long long fit = (full + s->ctx->sms - 1) / s->ctx->sms;
+        fit = std::min(fit, (s->sm_regs - regs) / std::max(1, fp.regs));
+        fit = std::min(fit, (s->sm_threads - threads) / std::max(1, fp.threads));
+        if (fp.smem > 0) fit = std::min(fit, (long long)((s->sm_smem - std::min(smem, s->sm_smem)) / fp.smem));
+        if (fit < 1) continue;
         Workspace* ws = make_workspace(g, s->mem, !plain, sl.stream, &st);
         void* d_dist = ws ? s->mem->alloc((size_t)k * g->n * 4) : nullptr;
         if (!ws || !d_dist) {
@@ -175,9 +178,8 @@ static bool try_launch(bfs_server* s) {
         }
         L.plain = plain;
         L.cta = fp;
-        const int32_t full = plain ? plain_grid_of(g) : g->grid_batch;
-        const int32_t grid = alone ? full : s->ctx->sms;
-        L.ctas_per_sm = (grid + s->ctx->sms - 1) / s->ctx->sms;
+        const int32_t grid = std::min<int32_t>(full, (int32_t)fit * s->ctx->sms);
+        L.ctas_per_sm = (int)fit;
         if (plain) {
             for (int i = 0; i < k && st == BFS_OK; ++i)
                 st = run_plain_on(g, ws, roots[i], static_cast<int32_t*>(d_dist) + (size_t)i * g->n,
