@@ -581,7 +581,8 @@ def gpu_arm(args, rank, world, local_rank):
             del dist, parent
             torch.cuda.empty_cache()
             line["batched_s24"] = batched_measure(24)
-            line["serving"] = serve_measure([18, 20, 22, 24], [1000, 10000], 0.5, 10000, 32)
+            line["serving"] = serve_measure([18, 20, 22, 24], [1000, 10000], 0.5, 10000, 32,
+                                            int8_rates=(10000,))
         print(json.dumps(line), flush=True)
 
 
@@ -694,7 +695,7 @@ def batched_arm(args):
 
 
 # --------------------------------------------------- serving configuration
-def serve_measure(scales, rates, window_s, max_queries, budget_gib, buf_gib=8.0):
+def serve_measure(scales, rates, window_s, max_queries, budget_gib, buf_gib=8.0, int8_rates=()):
     """Served single-root queries on resident Kronecker graphs (edge factor
     16, graph seed = scale; the scale-22 and scale-24 graphs are the headline
     and batched workloads' graphs): seeded Poisson arrivals at each offered
@@ -706,7 +707,9 @@ def serve_measure(scales, rates, window_s, max_queries, budget_gib, buf_gib=8.0)
     minus the scheduled arrival; the copy of the result row into the
     caller's pinned host buffer is inside it.  Baseline: the same trace run
     one query at a time by bfs_replay_single (bfs_run with a host row, in
-    arrival order, from a native thread), measured, not modelled."""
+    arrival order, from a native thread), measured, not modelled.  Rates in
+    int8_rates run again with int8 result rows (a quarter of the bytes to
+    copy to the host), the baseline with int8 rows too."""
     import torch
 
     import graphgen
@@ -726,9 +729,14 @@ def serve_measure(scales, rates, window_s, max_queries, budget_gib, buf_gib=8.0)
         nbuf = int(max(8, min(256, int(buf_gib * (1 << 30)) // (gr["n"] * 4))))
         gr["bufs"] = torch.empty((nbuf, gr["n"]), dtype=torch.int32, pin_memory=True).numpy()
         gr["base_bufs"] = gr["bufs"][:2]
+        if int8_rates:
+            nb8 = int(max(8, min(256, int(buf_gib * (1 << 30)) // gr["n"])))
+            gr["bufs8"] = torch.empty((nb8, gr["n"]), dtype=torch.int8, pin_memory=True).numpy()
+            gr["base_bufs8"] = gr["bufs8"][:2]
     handles = [gr["g"].handle for gr in graphs]
     results = []
-    for rate in rates:
+    for rate, rows in [(r, "int32") for r in rates] + [(r, "int8") for r in int8_rates]:
+        bkey, basekey = ("bufs8", "base_bufs8") if rows == "int8" else ("bufs", "base_bufs")
         nq = int(min(max_queries, rate * window_s))
         rng = np.random.default_rng(rate)
         gaps = rng.exponential(1.0 / rate, nq)
@@ -739,7 +747,7 @@ def serve_measure(scales, rates, window_s, max_queries, budget_gib, buf_gib=8.0)
         st0 = srv.stats()
         t0 = time.monotonic_ns() + 20_000_000
         arrival = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
-        done, status, _ = srv.replay(gid, rts, arrival, [gr["bufs"] for gr in graphs],
+        done, status, _ = srv.replay(gid, rts, arrival, [gr[bkey] for gr in graphs],
                                      timeout_us=120_000_000)
         st1 = srv.stats()
         errors = int(np.count_nonzero(status != bfs.BFS_OK))
@@ -749,11 +757,11 @@ def serve_measure(scales, rates, window_s, max_queries, budget_gib, buf_gib=8.0)
         t0 = time.monotonic_ns() + 20_000_000
         arrival_b = t0 + (np.cumsum(gaps) * 1e9).astype(np.int64)
         done_b, status_b = bfs.bfs_replay_single(handles, which.astype(np.int32), rts, arrival_b,
-                                                 [gr["base_bufs"] for gr in graphs])
+                                                 [gr[basekey] for gr in graphs])
         lat_b = (done_b - arrival_b) / 1e6
         launches = st1["launches"] - st0["launches"]
         results.append({
-            "offered_qps": rate, "queries": nq, "errors": errors,
+            "offered_qps": rate, "rows": rows, "queries": nq, "errors": errors,
             "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
             "sustained_qps": nq / span_s,
             "launches": int(launches),
@@ -785,7 +793,8 @@ def serve_arm(args):
     out = {"metric": METRIC, "data": "synthetic"}
     out.update(serve_measure([int(x) for x in args.serve_scales.split(",")],
                              [int(x) for x in args.serve_rates.split(",")], args.serve_window,
-                             args.serve_max_queries, args.serve_budget))
+                             args.serve_max_queries, args.serve_budget,
+                             int8_rates=[int(x) for x in args.serve_rates.split(",")][1:]))
     print(json.dumps(out), flush=True)
 
 

@@ -64,7 +64,8 @@ typedef int64_t bfs_ticket;
 #define BFS_UPLOAD_NO_RELABEL   0x2u  /* keep the caller's vertex order on device */
 /* bfs_run / bfs_run_batch */
 #define BFS_OUT_HOST            0x1u  /* outputs are host pointers (copied back, call waits) */
-#define BFS_DIST_INT8           0x2u  /* bfs_run_batch: int8 distances (levels <= 126) */
+#define BFS_DIST_INT8           0x2u  /* int8 distances (levels <= 126): bfs_run_batch,
+                                         bfs_run, bfs_submit_rows and the replays */
 #define BFS_HOST_LOOP           0x4u  /* one kernel launch per level, host reads the frontier
                                          size between levels (no device-side loop) */
 #define BFS_GRAPH_LOOP          0x8u  /* the level loop as a CUDA graph: init, seed, then a
@@ -216,7 +217,10 @@ bfs_status bfs_graph_autotune(bfs_graph* g, const int32_t* roots, int32_t nroots
 
 /* ---- single-source traversal ----------------------------------------------
  * Algorithm 1 / Algorithm 2 Phase 1 (one compute node) from `root` (caller
- * numbering).  dist: int32[n]; parent: int32[n] or NULL.  Device pointers by
+ * numbering).  dist: int32[n], or int8[n] with BFS_DIST_INT8 (the int32
+ * distances converted on the device; a level above 126 makes the traversal
+ * report BFS_ERR_DEPTH_OVERFLOW and is written as -2); parent: int32[n] or
+ * NULL.  Device pointers by
  * default (stream-ordered, returns after enqueueing); with BFS_OUT_HOST they
  * are host pointers and the call waits for completion.  Concurrent calls on
  * one graph must use the same stream (the graph's traversal buffers are
@@ -279,6 +283,13 @@ bfs_status bfs_server_create(bfs_context* ctx, size_t memory_budget, int32_t num
 bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id);
 bfs_status bfs_submit(bfs_server* s, int32_t graph_id, int32_t root, int32_t* dist_out,
                       bfs_ticket* ticket);
+/* bfs_submit with a choice of row type: flags = BFS_DIST_INT8 makes dist_out an
+ * int8[n] row (a quarter of the bytes to copy to the host; levels above 126
+ * fail the query with BFS_ERR_DEPTH_OVERFLOW, and the other queries of its
+ * launch with it), 0 an int32[n] row as bfs_submit.  int8 and int32 queries
+ * of one graph wait in separate FIFOs and never share a launch. */
+bfs_status bfs_submit_rows(bfs_server* s, int32_t graph_id, int32_t root, void* dist_out,
+                           uint32_t flags, bfs_ticket* ticket);
 /* BFS_PENDING while queued or running, BFS_OK once dist_out is written, or
  * the query's error.  A finished ticket can be polled until it is released. */
 bfs_status bfs_poll(bfs_server* s, bfs_ticket ticket);
@@ -319,20 +330,28 @@ bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids
                              int32_t* const* graph_bufs, const int32_t* bufs_per_graph,
                              int64_t timeout_us, int64_t* done_ns, int32_t* status_out,
                              int32_t* slot_out);
+/* bfs_server_replay with int8 rows when flags = BFS_DIST_INT8 (graph_bufs[g]
+ * then holds bufs_per_graph[g] rows of n_g int8; every query is submitted
+ * with bfs_submit_rows and those flags). */
+bfs_status bfs_server_replay_rows(bfs_server* s, int64_t nq, const int32_t* graph_ids,
+                                  const int32_t* roots, const int64_t* arrival_ns,
+                                  void* const* graph_bufs, const int32_t* bufs_per_graph,
+                                  uint32_t flags, int64_t timeout_us, int64_t* done_ns,
+                                  int32_t* status_out, int32_t* slot_out);
 /* The one-at-a-time baseline of a served trace: query i (graph
  * graphs[graph_ids[i]], root roots[i]) runs as bfs_run with a host output
  * row (BFS_OUT_HOST on `stream`) once arrival_ns[i] has come, strictly in
  * arrival order, from the calling thread -- each query waits for every
  * earlier one, as repeated plain single-source traversals on one GPU do.
  * Rows go to graph_bufs[g] (bufs_per_graph[g] consecutive rows of n_g int32,
- * used round robin).  done_ns[i] is the time bfs_run returned (steady
- * clock, as bfs_ticket_times), status_out[i] its status.  Returns the first
- * failure, if any. */
+ * or int8 with flags = BFS_DIST_INT8, used round robin).  done_ns[i] is the
+ * time bfs_run returned (steady clock, as bfs_ticket_times), status_out[i]
+ * its status.  Returns the first failure, if any. */
 bfs_status bfs_replay_single(bfs_graph* const* graphs, int32_t ngraphs, int64_t nq,
                              const int32_t* graph_ids, const int32_t* roots,
-                             const int64_t* arrival_ns, int32_t* const* graph_bufs,
-                             const int32_t* bufs_per_graph, void* stream, int64_t* done_ns,
-                             int32_t* status_out);
+                             const int64_t* arrival_ns, void* const* graph_bufs,
+                             const int32_t* bufs_per_graph, uint32_t flags, void* stream,
+                             int64_t* done_ns, int32_t* status_out);
 /* Stops the server; queued queries finish with BFS_ERR_CANCELLED. */
 bfs_status bfs_server_destroy(bfs_server* s);
 

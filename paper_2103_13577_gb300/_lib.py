@@ -123,6 +123,7 @@ SIGNATURES = {
     "bfs_server_create": (_i32, [_vp, _sz, _i32, _pp]),
     "bfs_server_add_graph": (_i32, [_vp, _vp, ctypes.POINTER(_i32)]),
     "bfs_submit": (_i32, [_vp, _i32, _i32, _vp, ctypes.POINTER(_i64)]),
+    "bfs_submit_rows": (_i32, [_vp, _i32, _i32, _vp, _u32, ctypes.POINTER(_i64)]),
     "bfs_poll": (_i32, [_vp, _i64]),
     "bfs_wait": (_i32, [_vp, _i64, _i64]),
     "bfs_release": (_i32, [_vp, _i64]),
@@ -130,7 +131,9 @@ SIGNATURES = {
                                 ctypes.POINTER(_i64)]),
     "bfs_server_get_stats": (_i32, [_vp, ctypes.POINTER(ServerStats)]),
     "bfs_server_replay": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _i64, _vp, _vp, _vp]),
-    "bfs_replay_single": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "bfs_server_replay_rows": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _u32, _i64, _vp, _vp,
+                                      _vp]),
+    "bfs_replay_single": (_i32, [_vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _u32, _vp, _vp, _vp]),
     "bfs_server_destroy": (_i32, [_vp]),
     "bfs_last_error": (ctypes.c_char_p, []),
     "bfs_status_string": (ctypes.c_char_p, [_i32]),

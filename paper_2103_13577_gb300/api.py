@@ -123,7 +123,8 @@ def bfs_graph_autotune(g: int, roots, batched: bool = False, cache_path: str | N
 
 
 def bfs_run(g: int, root: int, dist, parent=None, stream=None, flags: int = 0) -> None:
-    p_dist, dev = _buf(dist, np.int32)
+    flags |= _row_flags(dist)
+    p_dist, dev = _buf(dist)
     p_par, dev_p = _buf(parent, np.int32)
     if parent is not None and dev_p != dev:
         raise ValueError("dist and parent must both be host or both be device buffers")
@@ -258,12 +259,26 @@ def bfs_server_add_graph(s: int, g: int) -> int:
     return gid.value
 
 
+def _row_flags(buf) -> int:
+    """BFS_DIST_INT8 for int8 rows, 0 for int32 rows (numpy or torch)."""
+    dt = str(buf.dtype)
+    if dt in ("int8", "torch.int8"):
+        return BFS_DIST_INT8
+    if dt not in ("int32", "torch.int32"):
+        raise TypeError("rows must be int32 or int8")
+    return 0
+
+
 def bfs_submit(s: int, graph_id: int, root: int, dist_out) -> int:
-    p, dev = _buf(dist_out, np.int32)
+    """Queue a query; dist_out is a host row of int32 or int8 (then
+    submitted with BFS_DIST_INT8)."""
+    flags = _row_flags(dist_out)
+    p, dev = _buf(dist_out)
     if dev:
         raise ValueError("dist_out must be host memory")
     t = ctypes.c_int64()
-    check(_lib.lib().bfs_submit(s, graph_id, int(root), p, ctypes.byref(t)), "bfs_submit")
+    check(_lib.lib().bfs_submit_rows(s, graph_id, int(root), p, flags, ctypes.byref(t)),
+          "bfs_submit_rows")
     return t.value
 
 
@@ -295,18 +310,22 @@ def bfs_server_get_stats(s: int) -> dict:
 
 def bfs_server_replay(s: int, graph_ids, roots, arrival_ns, graph_bufs, timeout_us: int = -1):
     """Replay a query trace from native threads (see include/bfs.h).
-    graph_bufs: one C-contiguous int32 host array [k_g, n_g] per graph (pinned
-    memory keeps the copies fast).  Returns (done_ns, status, slot) arrays."""
+    graph_bufs: one C-contiguous host array [k_g, n_g] per graph, all int32 or
+    all int8 (then the queries ask for int8 rows; pinned memory keeps the
+    copies fast).  Returns (done_ns, status, slot) arrays."""
     gid = np.ascontiguousarray(graph_ids, dtype=np.int32)
     rts = np.ascontiguousarray(roots, dtype=np.int32)
     arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
     nq = len(gid)
     if len(rts) != nq or len(arr) != nq:
         raise ValueError("graph_ids, roots and arrival_ns must have the same length")
+    flags = {_row_flags(b) for b in graph_bufs}
+    if len(flags) != 1:
+        raise TypeError("replay buffers must all be int32 or all int8")
     ptrs = (ctypes.c_void_p * len(graph_bufs))()
     counts = np.zeros(len(graph_bufs), dtype=np.int32)
     for i, b in enumerate(graph_bufs):
-        p, dev = _buf(b, np.int32)
+        p, dev = _buf(b)
         if dev:
             raise ValueError("replay buffers are host memory")
         ptrs[i] = p
@@ -314,11 +333,12 @@ def bfs_server_replay(s: int, graph_ids, roots, arrival_ns, graph_bufs, timeout_
     done = np.zeros(nq, dtype=np.int64)
     status = np.zeros(nq, dtype=np.int32)
     slot = np.zeros(nq, dtype=np.int32)
-    check(_lib.lib().bfs_server_replay(s, nq, gid.ctypes.data, rts.ctypes.data, arr.ctypes.data,
-                                       ctypes.cast(ptrs, ctypes.c_void_p), counts.ctypes.data,
-                                       int(timeout_us), done.ctypes.data, status.ctypes.data,
-                                       slot.ctypes.data),
-          "bfs_server_replay")
+    check(_lib.lib().bfs_server_replay_rows(s, nq, gid.ctypes.data, rts.ctypes.data,
+                                            arr.ctypes.data, ctypes.cast(ptrs, ctypes.c_void_p),
+                                            counts.ctypes.data, flags.pop(), int(timeout_us),
+                                            done.ctypes.data, status.ctypes.data,
+                                            slot.ctypes.data),
+          "bfs_server_replay_rows")
     return done, status, slot
 
 
@@ -326,8 +346,9 @@ def bfs_replay_single(graphs, graph_ids, roots, arrival_ns, graph_bufs, stream=N
     """The one-at-a-time baseline of a served trace (see include/bfs.h):
     query i runs as bfs_run with a host output row once its arrival time has
     come, in arrival order, from a native thread.  graphs: graph handles;
-    graph_bufs: one C-contiguous int32 host array [k_g, n_g] per graph, used
-    round robin.  Returns (done_ns, status) arrays."""
+    graph_bufs: one C-contiguous host array [k_g, n_g] per graph, all int32 or
+    all int8 (int8 rows), used round robin.  Returns (done_ns, status)
+    arrays."""
     gid = np.ascontiguousarray(graph_ids, dtype=np.int32)
     rts = np.ascontiguousarray(roots, dtype=np.int32)
     arr = np.ascontiguousarray(arrival_ns, dtype=np.int64)
@@ -336,10 +357,13 @@ def bfs_replay_single(graphs, graph_ids, roots, arrival_ns, graph_bufs, stream=N
         raise ValueError("graph_ids, roots and arrival_ns must have the same length, "
                          "and one buffer array per graph")
     hs = (ctypes.c_void_p * len(graphs))(*graphs)
+    flags = {_row_flags(b) for b in graph_bufs}
+    if len(flags) != 1:
+        raise TypeError("replay buffers must all be int32 or all int8")
     ptrs = (ctypes.c_void_p * len(graph_bufs))()
     counts = np.zeros(len(graph_bufs), dtype=np.int32)
     for i, b in enumerate(graph_bufs):
-        p, dev = _buf(b, np.int32)
+        p, dev = _buf(b)
         if dev:
             raise ValueError("replay buffers are host memory")
         ptrs[i] = p
@@ -349,7 +373,8 @@ def bfs_replay_single(graphs, graph_ids, roots, arrival_ns, graph_bufs, stream=N
     check(_lib.lib().bfs_replay_single(ctypes.cast(hs, ctypes.c_void_p), len(graphs), nq,
                                        gid.ctypes.data, rts.ctypes.data, arr.ctypes.data,
                                        ctypes.cast(ptrs, ctypes.c_void_p), counts.ctypes.data,
-                                       _stream(stream), done.ctypes.data, status.ctypes.data),
+                                       flags.pop(), _stream(stream), done.ctypes.data,
+                                       status.ctypes.data),
           "bfs_replay_single")
     return done, status
 

@@ -170,6 +170,7 @@ void free_workspace(bfs_graph* g, Workspace* ws) {
     m->release(ws->lane_front);
     m->release(ws->lane_level);
     m->release(ws->dist_scratch);
+    m->release(ws->dist8_scratch);
     m->release(ws->parent_scratch);
     m->release(ws->batch_dist_scratch);
     delete ws;
@@ -874,7 +875,7 @@ bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* dist, int32_t* parent, v
                    uint32_t flags) {
     TraceRange tr("bfs_run", root);
     if (!g || !dist) return fail(BFS_ERR_INVALID_ARG, "null graph or dist");
-    if (flags & ~(BFS_OUT_HOST | BFS_HOST_LOOP | BFS_GRAPH_LOOP))
+    if (flags & ~(BFS_OUT_HOST | BFS_HOST_LOOP | BFS_GRAPH_LOOP | BFS_DIST_INT8))
         return fail(BFS_ERR_INVALID_ARG, "unknown flag");
     if ((flags & BFS_HOST_LOOP) && (flags & BFS_GRAPH_LOOP))
         return fail(BFS_ERR_INVALID_ARG, "BFS_HOST_LOOP and BFS_GRAPH_LOOP are exclusive");
@@ -886,21 +887,37 @@ bfs_status bfs_run(bfs_graph* g, int32_t root, int32_t* dist, int32_t* parent, v
     Workspace* ws = nullptr;
     bfs_status st = ensure_workspace(g, false, s, &ws);
     if (st != BFS_OK) return st;
+    const bool host = (flags & BFS_OUT_HOST) != 0;
+    const bool int8 = (flags & BFS_DIST_INT8) != 0;
+    // int32 distances go to the caller's buffer, or to staging when they are
+    // copied to the host or turned into int8 rows afterwards
     int32_t* d_dist = dist;
     int32_t* d_parent = parent;
-    const bool host = (flags & BFS_OUT_HOST) != 0;
-    if (host) {
+    int8_t* d_dist8 = int8 && !host ? reinterpret_cast<int8_t*>(dist) : nullptr;
+    if (host || int8) {
         if (!ws->dist_scratch) ws->dist_scratch = static_cast<int32_t*>(g->ctx->mem->alloc(g->n * 4));
+        if (!ws->dist_scratch) return fail(BFS_ERR_NO_MEMORY, "device memory exhausted (output staging)");
+        d_dist = ws->dist_scratch;
+    }
+    if (host) {
         if (parent && !ws->parent_scratch)
             ws->parent_scratch = static_cast<int32_t*>(g->ctx->mem->alloc(g->n * 4));
-        if (!ws->dist_scratch || (parent && !ws->parent_scratch))
+        if (int8 && !ws->dist8_scratch)
+            ws->dist8_scratch = static_cast<int8_t*>(g->ctx->mem->alloc(g->n + 16));
+        if ((parent && !ws->parent_scratch) || (int8 && !ws->dist8_scratch))
             return fail(BFS_ERR_NO_MEMORY, "device memory exhausted (output staging)");
-        d_dist = ws->dist_scratch;
         d_parent = parent ? ws->parent_scratch : nullptr;
+        if (int8) d_dist8 = ws->dist8_scratch;
     }
-    if ((st = run_plain_on(g, ws, root, d_dist, d_parent, s, flags, 0)) != BFS_OK) return st;
+    if ((st = run_plain_on(g, ws, root, d_dist, d_parent, s, flags & ~BFS_DIST_INT8, 0)) != BFS_OK)
+        return st;
+    if (int8) {
+        e = launch_dist_to_int8(d_dist, d_dist8, g->n, ws->stats, g->ctx->sms, s);
+        if (e != cudaSuccess) return cuda_fail(e, "int8 rows");
+    }
     if (!host) return BFS_OK;
-    e = cudaMemcpyAsync(dist, d_dist, g->n * 4, cudaMemcpyDeviceToHost, s);
+    if (int8) e = cudaMemcpyAsync(dist, d_dist8, g->n, cudaMemcpyDeviceToHost, s);
+    else e = cudaMemcpyAsync(dist, d_dist, g->n * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && parent)
         e = cudaMemcpyAsync(parent, d_parent, g->n * 4, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return cuda_fail(e, "result copy");

@@ -752,8 +752,10 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
 
 // Bin 0: 32 frontier vertices per warp, one per lane; their edges are laid
 // end to end by an exclusive scan and consumed 256 per round, lane l taking
-// edges l + 32 j (j < 8) and finding each edge's owner vertex by a
-// shuffle binary search over the scan.
+// edges l + 32 j (j < 8) and finding each edge's owner vertex in a
+// per-round owner table in shared memory that each lane fills for its own
+// edges (cheaper than a shuffle binary search per edge: a lane writes at
+// most its degree's slots).
 template <bool kBatch>
 __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, int cur,
                                    long long grp, long long cnt, int level, int nxt, int nslot) {
@@ -773,19 +775,23 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
     const int incl = warp_incl_scan(deg);
     const int excl = incl - deg;
     const int total = __shfl_sync(FULL_MASK, incl, 31);
+    // owner of each of the round's 256 edge slots, written by the owning lane
+    __shared__ uint8_t s_owner[kWarps][256];
+    uint8_t* const own = s_owner[threadIdx.x >> 5];
     for (int e0 = 0; e0 < total; e0 += 256) {
         unsigned okm = 0u;
         int32_t u[8], vv[8];
         uint64_t mm[8];
+        {
+            const int a = max(excl, e0), b = min(excl + deg, e0 + 256);
+            __syncwarp();
+            for (int e = a; e < b; ++e) own[e - e0] = (uint8_t)lane;
+            __syncwarp();
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int e = e0 + 32 * j + (int)lane;
-            int o = 0;
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) {
-                const int c = o + s;
-                if (__shfl_sync(FULL_MASK, excl, c & 31) <= e) o = c;
-            }
+            const int o = e < total ? own[32 * j + lane] : 0;
             const long long bo = __shfl_sync(FULL_MASK, base, o);
             const int xo = __shfl_sync(FULL_MASK, excl, o);
             vv[j] = __shfl_sync(FULL_MASK, v, o);
@@ -805,80 +811,6 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
 __device__ __forceinline__ unsigned unit_mask(int r, int lo, int hi) {
     const int a = min(max(lo - r, 0), 4), b = min(max(hi - r, 0), 4);
     return ((1u << b) - 1u) & ~((1u << a) - 1u);
-}
-
-// Column units through shared memory (BFS_ASYNC_COLS): round r + 1's units
-// are copied by cp.async (16 bytes per unit, L1 bypassed) into the warp's
-// second buffer while round r's are probed, so a round's column loads no
-// longer sit on its critical path and no registers hold them in flight.
-// Each lane reads back only the units it copied, so no warp barrier is
-// needed between the copies and the reads.  units: the warp's rows cut into
-// 16-byte units laid end to end (excl = exclusive prefix per lane, total =
-// all units); a4/rlo/rhi/v: the lane's row start (16-byte aligned), its
-// valid columns and vertex.
-#ifndef BFS_ASYNC_COLS
-#define BFS_ASYNC_COLS 0
-#endif
-constexpr bool kAsyncCols = BFS_ASYNC_COLS != 0;
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-__device__ __forceinline__ void cp_async_wait_one() {  // all but the newest group done
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
-}
-
-__device__ __forceinline__ void expand_units_async(const TraversalParams& P, Stage<false>& S,
-                                                   int total, int excl, long long a4, int rlo,
-                                                   int rhi, int32_t v, int level, int nxt,
-                                                   int nslot) {
-    __shared__ __align__(16) int4 s_units[kWarps][2][64];
-    const unsigned lane = lane_id();
-    int4 (*buf)[64] = s_units[threadIdx.x >> 5];
-    unsigned okm_n = 0u;
-    int32_t vo_n[2] = {0, 0};
-    // copy round q0's units into buffer b, keep their masks and vertices
-    auto issue = [&](int q0, int b) {
-        okm_n = 0u;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int q = q0 + 32 * h + (int)lane;
-            int o = 0;
-#pragma unroll
-            for (int st = 16; st > 0; st >>= 1) {
-                const int c = o + st;
-                if (__shfl_sync(FULL_MASK, excl, c & 31) <= q) o = c;
-            }
-            const long long a4o = __shfl_sync(FULL_MASK, a4, o);
-            const int lo_o = __shfl_sync(FULL_MASK, rlo, o);
-            const int hi_o = __shfl_sync(FULL_MASK, rhi, o);
-            const int xo = __shfl_sync(FULL_MASK, excl, o);
-            vo_n[h] = __shfl_sync(FULL_MASK, v, o);
-            if (q < total) {
-                const int r = 4 * (q - xo);
-                cp_async16(&buf[b][32 * h + lane], P.col + a4o + r);
-                okm_n |= unit_mask(r, lo_o, hi_o) << (4 * h);
-            }
-        }
-        cp_async_commit();
-    };
-    if (total > 0) issue(0, 0);
-    int b = 0;
-    for (int q0 = 0; q0 < total; q0 += 64, b ^= 1) {
-        const unsigned okm = okm_n;
-        const int32_t v0 = vo_n[0], v1 = vo_n[1];
-        if (q0 + 64 < total) issue(q0 + 64, b ^ 1);
-        else cp_async_commit();  // an empty group keeps "all but the newest" meaning this round
-        cp_async_wait_one();
-        const int4 x0 = buf[b][lane], x1 = buf[b][32 + lane];
-        const int32_t u[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
-        const int32_t vv[8] = {v0, v0, v0, v0, v1, v1, v1, v1};
-        visit_plain_k<8>(P, S, okm, u, vv, level, nxt, nslot);
-    }
 }
 
 // Bin 1: one warp per chunk of chunk_warp edges.  The chunk's vertex
@@ -920,12 +852,6 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
         const int incl = warp_incl_scan(units);
         const int excl = incl - units;
         const int total = __shfl_sync(FULL_MASK, incl, 31);
-        if constexpr (!kBatch && kAsyncCols) {
-            expand_units_async(P, S, total, excl, a4, rlo, rhi, v, level, nxt, nslot);
-            if (__popc(okb) < 32) break;
-            i += 32;
-            continue;
-        }
         for (int q0 = 0; q0 < total; q0 += 64) {
             unsigned okm = 0u;
             int32_t u[8], vv[8];
@@ -1247,10 +1173,6 @@ __device__ void expand_bitmap_tile(const TraversalParams& P, Stage<false>& S, lo
         const int incl = warp_incl_scan(units);
         const int excl = incl - units;
         const int total = __shfl_sync(FULL_MASK, incl, 31);
-        if constexpr (kAsyncCols) {
-            expand_units_async(P, S, total, excl, a4, rlo, rhi, v, level, nxt, nslot);
-            continue;
-        }
         for (int q0 = 0; q0 < total; q0 += 64) {
             unsigned okm = 0u;
             int32_t u[8], vv[8];
@@ -2035,6 +1957,47 @@ const void* batch_persistent_fn(int mb) {
 }
 const void* batch_step_fn(int mb) {
     return mb >= 3 ? (const void*)bfs_batch_step<3> : (const void*)bfs_batch_step<2>;
+}
+
+// int8 rows from int32 distances, 16 per thread and step (16-byte loads and
+// stores when both arrays are 16-byte aligned, else one at a time).
+__global__ void dist_to_int8_kernel(const int32_t* __restrict__ src, int8_t* __restrict__ dst,
+                                    long long count, DevStats* stats, bool vec) {
+    const long long nthreads = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n16 = vec ? count / 16 : 0;   // 16-byte accesses need aligned ends
+    bool deep = false;
+    for (long long i = tid; i < n16; i += nthreads) {
+        const int4* s4 = reinterpret_cast<const int4*>(src + 16 * i);
+        unsigned w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int4 x = __ldcs(s4 + k);
+            const int v[4] = {x.x, x.y, x.z, x.w};
+            unsigned b = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                int y = v[c];
+                if (y > 126) { deep = true; y = -2; }
+                b |= (unsigned)(uint8_t)(int8_t)y << (8 * c);
+            }
+            w[k] = b;
+        }
+        reinterpret_cast<uint4*>(dst)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    for (long long i = 16 * n16 + tid; i < count; i += nthreads) {
+        int y = src[i];
+        if (y > 126) { deep = true; y = -2; }
+        dst[i] = (int8_t)y;
+    }
+    if (deep && stats) atomicCAS(&stats->status, 0, (int)kDevDepth);
+}
+
+cudaError_t launch_dist_to_int8(const int32_t* src, int8_t* dst, long long count, DevStats* stats,
+                                int sms, cudaStream_t s) {
+    const bool vec = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15u) == 0;
+    dist_to_int8_kernel<<<sms * 4, 256, 0, s>>>(src, dst, count, stats, vec);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_csr_check(const int64_t* off, const int32_t* col, long long n, long long nnz,

@@ -53,6 +53,7 @@ struct Workspace {
     uint8_t* lane_level = nullptr;     // batched: [n][64] level bytes
     int32_t* roots = nullptr;          // [64]
     int32_t* dist_scratch = nullptr;   // host-output staging (plain: n; batched: none)
+    int8_t* dist8_scratch = nullptr;   // plain int8 rows with host output: n bytes
     int32_t* parent_scratch = nullptr;
     void* batch_dist_scratch = nullptr;  // batched host-output staging, 64 * n int32
     DeviceAllocator* mem = nullptr;    // where the buffers came from
@@ -154,4 +155,8 @@ struct CtaFootprint {
     size_t smem = 0;
 };
 bfs_status cta_footprint(const bfs_graph* g, bool batched, CtaFootprint* out);
+// int8 copy of k rows of n int32 distances (-1 stays -1); a distance above
+// 126 records kDevDepth in stats (when not null) and is written as -2
+cudaError_t launch_dist_to_int8(const int32_t* src, int8_t* dst, long long count, DevStats* stats,
+                                int sms, cudaStream_t s);
 }  // namespace bfs

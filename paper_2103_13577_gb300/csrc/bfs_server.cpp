@@ -41,7 +41,8 @@ struct Query {
     bfs_ticket ticket = 0;
     int32_t graph_id = 0;
     int32_t root = 0;
-    int32_t* dist_out = nullptr;
+    void* dist_out = nullptr;    // int32[n], or int8[n] for an int8 query
+    bool int8 = false;
     bfs_status status = BFS_PENDING;
     int64_t submit_ns = 0, launch_ns = 0, done_ns = 0;
 };
@@ -54,6 +55,7 @@ struct Launch {
     CtaFootprint cta;        // what one of them holds
     Workspace* ws = nullptr;
     void* d_dist = nullptr;
+    void* d_dist8 = nullptr;   // int8 rows of a single-source launch of int8 queries
     std::vector<std::shared_ptr<Query>> lanes;
     cudaEvent_t done = nullptr;
 };
@@ -85,7 +87,7 @@ struct bfs_server {
     DeviceAllocator* mem = nullptr;
     std::vector<bfs_graph*> graphs;
     std::vector<GraphPolicy> policy;
-    std::vector<std::deque<std::shared_ptr<Query>>> pending;
+    std::vector<std::deque<std::shared_ptr<Query>>> pending;  // [2 graph + int8]: FIFOs
     std::unordered_map<bfs_ticket, std::shared_ptr<Query>> tickets;
     std::vector<SlotState> slots;
     std::vector<Launch> inflight;
@@ -120,10 +122,12 @@ static bool try_launch(bfs_server* s) {
             break;
         }
     if (free_slot < 0) return false;
-    const size_t ng = s->graphs.size();
-    for (size_t t = 0; t < ng; ++t) {
-        const size_t gid = (s->rr + t) % ng;
-        auto& q = s->pending[gid];
+    const size_t nq = s->pending.size();   // two per graph: int32 and int8 rows
+    for (size_t t = 0; t < nq; ++t) {
+        const size_t qi = (s->rr + t) % nq;
+        const size_t gid = qi / 2;
+        const bool int8 = (qi & 1) != 0;
+        auto& q = s->pending[qi];
         if (q.empty()) continue;
         bfs_graph* g = s->graphs[gid];
         const int k = (int)std::min<size_t>(64, q.size());
@@ -157,10 +161,17 @@ static bool try_launch(bfs_server* s) {
         if (fp.smem > 0) fit = std::min(fit, (long long)((s->sm_smem - std::min(smem, s->sm_smem)) / fp.smem));
         if (fit < 1) continue;
         Workspace* ws = make_workspace(g, s->mem, !plain, sl.stream, &st);
-        void* d_dist = ws ? s->mem->alloc((size_t)k * g->n * 4) : nullptr;
-        if (!ws || !d_dist) {
+        // distance rows: int32 (single-source runs, or an int32 batch), int8
+        // for a batch of int8 queries; single-source int8 queries also get
+        // int8 rows converted from the int32 ones
+        const size_t rows = (size_t)k * g->n;
+        void* d_dist = ws ? s->mem->alloc(int8 && !plain ? rows + 16 : rows * 4) : nullptr;
+        void* d_dist8 = (ws && int8 && plain) ? s->mem->alloc(rows + 16) : nullptr;
+        if (!ws || !d_dist || (int8 && plain && !d_dist8)) {
             if (ws) free_workspace(g, ws);
-            continue;  // does not fit now; another graph might, or wait for completions
+            s->mem->release(d_dist);
+            s->mem->release(d_dist8);
+            continue;  // does not fit now; another queue might, or wait for completions
         }
         TraceRange tr("server_launch", k);
         Launch L;
@@ -168,6 +179,7 @@ static bool try_launch(bfs_server* s) {
         L.graph_id = (int32_t)gid;
         L.ws = ws;
         L.d_dist = d_dist;
+        L.d_dist8 = d_dist8;
         std::vector<int32_t> roots;
         const int64_t t_launch = now_ns();
         for (int i = 0; i < k; ++i) {
@@ -184,18 +196,26 @@ static bool try_launch(bfs_server* s) {
             for (int i = 0; i < k && st == BFS_OK; ++i)
                 st = run_plain_on(g, ws, roots[i], static_cast<int32_t*>(d_dist) + (size_t)i * g->n,
                                   nullptr, sl.stream, 0, grid);
+            if (st == BFS_OK && int8) {
+                cudaError_t e = launch_dist_to_int8(static_cast<int32_t*>(d_dist),
+                                                    static_cast<int8_t*>(d_dist8), (long long)rows,
+                                                    ws->stats, s->ctx->sms, sl.stream);
+                if (e != cudaSuccess) st = cuda_fail(e, "int8 rows");
+            }
         } else {
-            st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, 0, grid);
+            st = run_batch_on(g, ws, roots.data(), k, d_dist, sl.stream, int8 ? BFS_DIST_INT8 : 0,
+                              grid);
         }
         if (st == BFS_OK) {
             cudaError_t e = cudaEventRecord(sl.kevent, sl.stream);
             if (e != cudaSuccess) st = cuda_fail(e, "event record");
         }
         if (st == BFS_OK) {
+            const char* src = static_cast<const char*>(int8 ? (plain ? d_dist8 : d_dist) : d_dist);
+            const size_t row = (size_t)g->n * (int8 ? 1 : 4);
             for (int i = 0; i < k; ++i) {
-                cudaError_t e = cudaMemcpyAsync(L.lanes[i]->dist_out,
-                                                static_cast<int32_t*>(d_dist) + (size_t)i * g->n,
-                                                (size_t)g->n * 4, cudaMemcpyDeviceToHost, sl.stream);
+                cudaError_t e = cudaMemcpyAsync(L.lanes[i]->dist_out, src + (size_t)i * row, row,
+                                                cudaMemcpyDeviceToHost, sl.stream);
                 if (e != cudaSuccess) {
                     st = cuda_fail(e, "result copy");
                     break;
@@ -212,6 +232,7 @@ static bool try_launch(bfs_server* s) {
             s->stats.failed += k;
             free_workspace(g, ws);
             s->mem->release(d_dist);
+            s->mem->release(d_dist8);
             s->cv_done.notify_all();
             return true;
         }
@@ -223,7 +244,7 @@ static bool try_launch(bfs_server* s) {
         s->stats.max_inflight_bytes =
             std::max<int64_t>(s->stats.max_inflight_bytes, (int64_t)s->inflight_bytes);
         s->inflight.push_back(std::move(L));
-        s->rr = (gid + 1) % ng;
+        s->rr = (qi + 1) % nq;
         return true;
     }
     return false;
@@ -251,6 +272,7 @@ static int reap(bfs_server* s, bool block) {
         else s->stats.failed += (int64_t)L.lanes.size();
         free_workspace(s->graphs[L.graph_id], L.ws);
         s->mem->release(L.d_dist);
+        s->mem->release(L.d_dist8);
         s->slots[L.slot].busy = false;
         s->inflight.erase(s->inflight.begin() + (long)i);
         ++n;
@@ -283,12 +305,12 @@ static void dispatcher_main(bfs_server* s) {
             });
         } else if (!progressed) {
             // queries wait but nothing fits and nothing is in flight: they can never run
-            for (size_t gid = 0; gid < s->pending.size(); ++gid) {
-                for (auto& q : s->pending[gid]) {
+            for (auto& fifo : s->pending) {
+                for (auto& q : fifo) {
                     q->status = BFS_ERR_BUDGET;
                     s->stats.failed += 1;
                 }
-                s->pending[gid].clear();
+                fifo.clear();
             }
             s->cv_done.notify_all();
         }
@@ -423,15 +445,20 @@ bfs_status bfs_server_add_graph(bfs_server* s, bfs_graph* g, int32_t* graph_id) 
     std::lock_guard<std::mutex> lk(s->mu);
     s->graphs.push_back(g);
     s->policy.push_back(pol);
-    s->pending.emplace_back();
+    s->pending.emplace_back();   // int32 rows
+    s->pending.emplace_back();   // int8 rows
     *graph_id = (int32_t)s->graphs.size() - 1;
     return BFS_OK;
 }
 
-bfs_status bfs_submit(bfs_server* s, int32_t graph_id, int32_t root, int32_t* dist_out,
-                      bfs_ticket* ticket) {
+bfs_status bfs_submit_rows(bfs_server* s, int32_t graph_id, int32_t root, void* dist_out,
+                           uint32_t flags, bfs_ticket* ticket) {
     if (!s || !dist_out || !ticket) {
         set_error("null argument");
+        return BFS_ERR_INVALID_ARG;
+    }
+    if (flags & ~BFS_DIST_INT8) {
+        set_error("unknown flag");
         return BFS_ERR_INVALID_ARG;
     }
     std::lock_guard<std::mutex> lk(s->mu);
@@ -457,13 +484,19 @@ bfs_status bfs_submit(bfs_server* s, int32_t graph_id, int32_t root, int32_t* di
     q->graph_id = graph_id;
     q->root = root;
     q->dist_out = dist_out;
+    q->int8 = (flags & BFS_DIST_INT8) != 0;
     q->submit_ns = now_ns();
     s->tickets[q->ticket] = q;
-    s->pending[(size_t)graph_id].push_back(q);
+    s->pending[2 * (size_t)graph_id + (q->int8 ? 1 : 0)].push_back(q);
     s->stats.submitted += 1;
     *ticket = q->ticket;
     s->cv_work.notify_one();
     return BFS_OK;
+}
+
+bfs_status bfs_submit(bfs_server* s, int32_t graph_id, int32_t root, int32_t* dist_out,
+                      bfs_ticket* ticket) {
+    return bfs_submit_rows(s, graph_id, root, dist_out, 0, ticket);
 }
 
 bfs_status bfs_poll(bfs_server* s, bfs_ticket ticket) {
@@ -536,16 +569,21 @@ bfs_status bfs_release(bfs_server* s, bfs_ticket ticket) {
     return BFS_OK;
 }
 
-bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids,
-                             const int32_t* roots, const int64_t* arrival_ns,
-                             int32_t* const* graph_bufs, const int32_t* bufs_per_graph,
-                             int64_t timeout_us, int64_t* done_ns, int32_t* status_out,
-                             int32_t* slot_out) {
+bfs_status bfs_server_replay_rows(bfs_server* s, int64_t nq, const int32_t* graph_ids,
+                                  const int32_t* roots, const int64_t* arrival_ns,
+                                  void* const* graph_bufs, const int32_t* bufs_per_graph,
+                                  uint32_t flags, int64_t timeout_us, int64_t* done_ns,
+                                  int32_t* status_out, int32_t* slot_out) {
     if (!s || nq < 0 || (nq > 0 && (!graph_ids || !roots || !arrival_ns || !graph_bufs ||
                                     !bufs_per_graph || !done_ns || !status_out))) {
         set_error("null argument");
         return BFS_ERR_INVALID_ARG;
     }
+    if (flags & ~BFS_DIST_INT8) {
+        set_error("unknown flag");
+        return BFS_ERR_INVALID_ARG;
+    }
+    const size_t elt = (flags & BFS_DIST_INT8) ? 1 : 4;
     std::vector<int64_t> ns;  // vertices per graph
     {
         std::lock_guard<std::mutex> lk(s->mu);
@@ -665,8 +703,8 @@ bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids
                     std::this_thread::sleep_for(std::chrono::nanoseconds(arrival_ns[i] - now - 100000));
             }
             bfs_ticket t = 0;
-            const bfs_status st =
-                bfs_submit(s, g, roots[i], graph_bufs[g] + (size_t)slot * (size_t)ns[(size_t)g], &t);
+            char* row = static_cast<char*>(graph_bufs[g]) + (size_t)slot * (size_t)ns[(size_t)g] * elt;
+            const bfs_status st = bfs_submit_rows(s, g, roots[i], row, flags, &t);
             std::lock_guard<std::mutex> lk(mu);
             if (st != BFS_OK) {
                 first_err = st;
@@ -698,17 +736,32 @@ bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids
     return BFS_OK;
 }
 
+bfs_status bfs_server_replay(bfs_server* s, int64_t nq, const int32_t* graph_ids,
+                             const int32_t* roots, const int64_t* arrival_ns,
+                             int32_t* const* graph_bufs, const int32_t* bufs_per_graph,
+                             int64_t timeout_us, int64_t* done_ns, int32_t* status_out,
+                             int32_t* slot_out) {
+    return bfs_server_replay_rows(s, nq, graph_ids, roots, arrival_ns,
+                                  reinterpret_cast<void* const*>(graph_bufs), bufs_per_graph, 0,
+                                  timeout_us, done_ns, status_out, slot_out);
+}
+
 bfs_status bfs_replay_single(bfs_graph* const* graphs, int32_t ngraphs, int64_t nq,
                              const int32_t* graph_ids, const int32_t* roots,
-                             const int64_t* arrival_ns, int32_t* const* graph_bufs,
-                             const int32_t* bufs_per_graph, void* stream, int64_t* done_ns,
-                             int32_t* status_out) {
+                             const int64_t* arrival_ns, void* const* graph_bufs,
+                             const int32_t* bufs_per_graph, uint32_t flags, void* stream,
+                             int64_t* done_ns, int32_t* status_out) {
     if (!graphs || ngraphs < 1 || nq < 0 ||
         (nq > 0 && (!graph_ids || !roots || !arrival_ns || !graph_bufs || !bufs_per_graph ||
                     !done_ns || !status_out))) {
         set_error("null argument");
         return BFS_ERR_INVALID_ARG;
     }
+    if (flags & ~BFS_DIST_INT8) {
+        set_error("unknown flag");
+        return BFS_ERR_INVALID_ARG;
+    }
+    const size_t elt = (flags & BFS_DIST_INT8) ? 1 : 4;
     for (int64_t i = 0; i < nq; ++i) {
         const int g = graph_ids[i];
         if (g < 0 || g >= ngraphs || !graphs[g] || bufs_per_graph[g] < 1 || !graph_bufs[g]) {
@@ -726,9 +779,10 @@ bfs_status bfs_replay_single(bfs_graph* const* graphs, int32_t ngraphs, int64_t 
             if (arrival_ns[i] - now > 200000)
                 std::this_thread::sleep_for(std::chrono::nanoseconds(arrival_ns[i] - now - 100000));
         }
-        int32_t* out = graph_bufs[g] + (size_t)(used[(size_t)g]++ % bufs_per_graph[g]) *
-                                           (size_t)graphs[g]->n;
-        const bfs_status st = bfs_run(graphs[g], roots[i], out, nullptr, stream, BFS_OUT_HOST);
+        char* out = static_cast<char*>(graph_bufs[g]) +
+                    (size_t)(used[(size_t)g]++ % bufs_per_graph[g]) * (size_t)graphs[g]->n * elt;
+        const bfs_status st = bfs_run(graphs[g], roots[i], reinterpret_cast<int32_t*>(out), nullptr,
+                                      stream, BFS_OUT_HOST | (flags & BFS_DIST_INT8));
         done_ns[i] = now_ns();
         status_out[i] = st;
         if (st != BFS_OK && first_err == BFS_OK) first_err = st;

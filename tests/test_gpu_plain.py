@@ -423,3 +423,45 @@ def test_tma_staged_heavy_runs(ctx, kron16, bins):
     with pytest.raises(bfs.BfsError):
         g.set_option(bfs.BFS_OPT_TMA_STAGE, 3)
     g.close()
+
+
+def test_int8_rows(ctx, kron16):
+    """BFS_DIST_INT8: the same distances as int8, to device memory (aligned
+    and at an odd offset, which takes the one-at-a-time conversion) and to
+    host memory, with parents still int32."""
+    off, col, roots = kron16
+    n = len(off) - 1
+    g = bfs.Graph(ctx, off, col)
+    for r in roots[:4]:
+        r = int(r)
+        ref = oracle.bfs(off, col, r)[0]
+        d8 = torch.full((n + 3,), 99, dtype=torch.int8, device="cuda")
+        p = torch.empty(n, dtype=torch.int32, device="cuda")
+        g.run(r, d8[:n], p)
+        assert g.sync()["status"] == 0
+        assert np.array_equal(d8[:n].cpu().numpy().astype(np.int32), ref)
+        assert oracle.check_bfs(off, col, r, d8[:n].cpu().numpy(), p.cpu().numpy())["ok"]
+        g.run(r, d8[3:])                      # 3-byte offset: not 16-byte aligned
+        g.sync()
+        assert np.array_equal(d8[3:].cpu().numpy().astype(np.int32), ref)
+        h8 = np.full(n, 99, dtype=np.int8)
+        hp = np.empty(n, dtype=np.int32)
+        g.run(r, h8, hp)
+        assert np.array_equal(h8.astype(np.int32), ref)
+        assert oracle.check_bfs(off, col, r, h8, hp)["ok"]
+    g.close()
+
+
+def test_int8_rows_depth_overflow(ctx):
+    """A path of 200 vertices has levels up to 199: int8 rows cannot hold
+    them, and the call says so instead of wrapping."""
+    off, col = G.path(200)
+    g = bfs.Graph(ctx, off, col)
+    h8 = np.empty(200, dtype=np.int8)
+    with pytest.raises(bfs.BfsError) as e:
+        g.run(0, h8)
+    assert e.value.status == bfs.BFS_ERR_DEPTH_OVERFLOW
+    d = np.empty(200, dtype=np.int32)
+    g.run(0, d)                               # int32 rows still fine afterwards
+    assert np.array_equal(d, np.arange(200, dtype=np.int32))
+    g.close()

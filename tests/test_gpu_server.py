@@ -122,3 +122,59 @@ def test_native_replay(setup):
             assert np.array_equal(bufs[gi][sl], ref)
     assert srv.stats()["completed"] == nq
     srv.close()
+
+
+def test_int8_and_int32_rows_in_one_stream(setup):
+    """Queries asking for int8 rows (bfs_submit_rows with BFS_DIST_INT8) and
+    for int32 rows, interleaved in one burst on three graphs: each row equals
+    the oracle's distances, whichever launch and row type carried it."""
+    ctx, graphs = setup
+    srv = bfs.Server(ctx, 512 << 20, num_streams=3)
+    gids = [srv.add_graph(g) for _, _, g in graphs]
+    rng = np.random.default_rng(11)
+    plan = []
+    for i in range(120):
+        gi = int(rng.integers(0, len(graphs)))
+        off = graphs[gi][0]
+        root = int(graphgen.pick_roots(off, 1, seed=3000 + i)[0])
+        dt = torch.int8 if i % 2 else torch.int32
+        out = torch.full((len(off) - 1,), -7, dtype=dt).pin_memory().numpy()
+        plan.append((gi, root, out, srv.submit(gids[gi], root, out)))
+    for gi, root, out, t in plan:
+        assert srv.wait(t, 30_000_000) == bfs.BFS_OK
+        off, col, _ = graphs[gi]
+        assert np.array_equal(out.astype(np.int32), oracle.bfs(off, col, root)[0])
+        srv.release(t)
+    st = srv.stats()
+    assert st["completed"] == 120 and st["launches"] < 120
+    srv.close()
+
+
+def test_replays_with_int8_rows(setup):
+    """The native replay and the one-at-a-time baseline with int8 rows."""
+    ctx, graphs = setup
+    srv = bfs.Server(ctx, 512 << 20, num_streams=3)
+    gids = np.array([srv.add_graph(g) for _, _, g in graphs], dtype=np.int32)
+    rng = np.random.default_rng(5)
+    nq = 60
+    which = rng.integers(0, len(graphs), nq).astype(np.int32)
+    roots = np.array([int(graphgen.pick_roots(graphs[w][0], 1, seed=4000 + i)[0])
+                      for i, w in enumerate(which)], dtype=np.int32)
+    counts = np.bincount(which, minlength=len(graphs))
+    arrival = time.monotonic_ns() + 5_000_000 + np.cumsum(rng.exponential(50_000, nq)).astype(np.int64)
+    bufs = [np.full((int(c) + 1, len(off) - 1), -7, dtype=np.int8) for c, (off, _, _) in
+            zip(counts, graphs)]
+    done, status, slot = srv.replay(gids[which], roots, arrival, bufs, timeout_us=30_000_000)
+    assert np.all(status == bfs.BFS_OK)
+    srv.close()
+    arrival = time.monotonic_ns() + 5_000_000 + np.cumsum(rng.exponential(50_000, nq)).astype(np.int64)
+    one = [np.full((1, len(off) - 1), -7, dtype=np.int8) for off, _, _ in graphs]
+    done1, status1 = bfs.bfs_replay_single([g.handle for _, _, g in graphs], which, roots,
+                                           arrival, one)
+    assert np.all(status1 == bfs.BFS_OK) and np.all(done1 >= arrival)
+    # the last query of each graph is the one left in its single row
+    for gi, (off, col, _) in enumerate(graphs):
+        mine = np.nonzero(which == gi)[0]
+        if len(mine):
+            last = mine[-1]
+            assert np.array_equal(one[gi][0].astype(np.int32), oracle.bfs(off, col, int(roots[last]))[0])
