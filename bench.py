@@ -216,7 +216,7 @@ def paths_measure(bfs, torch, dev_, stream, off, col, roots, n):
     next-frontier marks, the sigma additions and the per-level bitmap scans
     (N / 8 bytes) are cache traffic, not counted."""
     peak, _ = measured_hbm_peak()
-    arena = torch.empty(int(32 * n + (64 << 20)), dtype=torch.uint8, device=dev_)
+    arena = torch.empty(int(64 * n + (64 << 20)), dtype=torch.uint8, device=dev_)
     pctx = bfs.Context(dev_.index, arena=arena)
     d_off = torch.from_numpy(np.ascontiguousarray(off, dtype=np.int64)).to(dev_)
     d_col = torch.from_numpy(np.ascontiguousarray(col, dtype=np.int32)).to(dev_)
