@@ -31,9 +31,9 @@ struct LevelCtl {
 };
 
 struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
-    unsigned int pad[30];
+    unsigned long long arrived;   // arrivals since the launch began; bit 63: a CTA gave up
+    unsigned int exited;          // CTAs that have left the launch
+    unsigned int pad[29];
 };
 
 struct DevStats {

@@ -148,40 +148,56 @@ __device__ __forceinline__ bool mbar_wait_bounded(const TraversalParams& P,
 }
 
 // ------------------------------------------------------------ grid barrier
-// All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA
-// arrives on a counter; the last arrival resets it and bumps a generation
-// word that the others poll with acquire loads.  The poll gives up after
-// timeout_ns of %globaltimer, records kDevTimeout and returns false; it also
-// returns false as soon as another CTA has recorded a failure.
-__device__ bool grid_barrier(const TraversalParams& P) {
+// All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA adds
+// its arrival to one 64-bit word that only grows during a launch: the k-th
+// barrier is complete once the word reaches k * gridDim.x, so an arrival is
+// a fire-and-forget reduction and the wait is a loop of acquire loads (no
+// reset or generation step that the last arrival would have to publish with
+// further round trips).  Bit 63 of the word says that a CTA gave up: a wait
+// longer than timeout_ns of %globaltimer records kDevTimeout, sets the bit
+// and returns false, and every CTA that reads the bit returns false too.
+// `epoch` (thread 0's, in shared memory: no register held across the level
+// loop) counts the barriers this CTA has passed in the launch, the same in
+// every CTA; the last CTA to leave the launch clears the word.
+constexpr unsigned long long kBarGaveUp = 1ull << 63;
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Tells every CTA waiting at (or arriving at) a grid barrier to leave.
+__device__ __forceinline__ void give_up(const TraversalParams& P) {
+    atomicExch(&P.stats->abort, 1);
+    atomicOr(&P.bar->arrived, kBarGaveUp);
+}
+
+__device__ bool grid_barrier(const TraversalParams& P, unsigned long long& epoch) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        GridBarrier* B = P.bar;
-        int ok = 1;
-        const unsigned g = ld_acquire_u32(&B->gen);
+        unsigned long long* const word = &P.bar->arrived;
+        const unsigned long long target =
+            ++epoch * gridDim.x + (P.debug_stall ? 1ull : 0ull);
         __threadfence();
-        const unsigned target = gridDim.x + (P.debug_stall ? 1u : 0u);
-        const unsigned arrived = atomicAdd(&B->count, 1u) + 1u;
-        if (arrived == target) {
-            atomicExch(&B->count, 0u);
-            __threadfence();
-            st_release_u32(&B->gen, g + 1u);
-        } else {
-            const unsigned long long t0 = global_timer_ns();
-            while (ld_acquire_u32(&B->gen) == g) {
-                if (ld_volatile_i32(&P.stats->abort) != 0) { ok = 0; break; }
-                if (global_timer_ns() - t0 > (unsigned long long)P.timeout_ns) {
-                    raise_status(P, kDevTimeout);
-                    atomicExch(&P.stats->abort, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(word) : "memory");
+        int ok = 1;
+        unsigned long long t0 = 0ull;
+        for (;;) {
+            const unsigned long long a = ld_acquire_u64(word);
+            if (a & kBarGaveUp) { ok = 0; break; }
+            if (a >= target) break;
+            const unsigned long long t = global_timer_ns();
+            if (t0 == 0ull) {
+                t0 = t;
+            } else if (t - t0 > (unsigned long long)P.timeout_ns) {
+                raise_status(P, kDevTimeout);
+                give_up(P);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
-        if (ld_volatile_i32(&P.stats->abort) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -194,10 +210,10 @@ __device__ void kernel_exit(const TraversalParams& P) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        const unsigned done = atomicAdd(&P.bar->pad[0], 1u) + 1u;
+        const unsigned done = atomicAdd(&P.bar->exited, 1u) + 1u;
         if (done == gridDim.x) {
-            atomicExch(&P.bar->count, 0u);
-            atomicExch(&P.bar->pad[0], 0u);
+            atomicExch(&P.bar->arrived, 0ull);
+            atomicExch(&P.bar->exited, 0u);
             atomicExch(&P.stats->abort, 0);
             __threadfence();
         }
@@ -278,6 +294,15 @@ __device__ __forceinline__ void stage_flush(const TraversalParams& P, Stage<kBat
     int deg[H];
 #pragma unroll
     for (int h = 0; h < H; ++h) u[h] = (i0 + h < n) ? S.u[i0 + h] : -1;
+    // The random reads that do not depend on the claim (row offsets, caller
+    // numbering) are issued before it, so that their round trip overlaps the
+    // atomics' instead of following it.
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        deg[h] = -1;
+        if (u[h] >= 0) deg[h] = (int)(__ldg(off + u[h] + 1) - __ldg(off + u[h]));
+    }
+    int32_t cu[H], cv[H];
     // Plain entries are candidates (their target looked unvisited when it
     // was probed): the claim -- an atomicOr on the visited bitmap whose old
     // value says who set the bit first -- happens here, for all of a flush's
@@ -287,7 +312,15 @@ __device__ __forceinline__ void stage_flush(const TraversalParams& P, Stage<kBat
     if constexpr (!kBatch) {
         uint32_t* const visited = P.visited;
 #pragma unroll
-        for (int h = 0; h < H; ++h) pv[h] = u[h] >= 0 ? (uint32_t)S.v[i0 + h] : 0u;
+        for (int h = 0; h < H; ++h) {
+            pv[h] = u[h] >= 0 ? (uint32_t)S.v[i0 + h] : 0u;
+            cu[h] = u[h];
+            cv[h] = (u[h] >= 0) ? (int32_t)(pv[h] & ~kClaimed) : 0;
+            if (new2old && u[h] >= 0) {
+                cu[h] = __ldg(new2old + u[h]);
+                cv[h] = __ldg(new2old + cv[h]);
+            }
+        }
         if (P.use_match_any) {
             // lanes claiming bits of the same word merge them: one atomicOr
             // per word, the first lane holding a vertex wins it
@@ -317,11 +350,6 @@ __device__ __forceinline__ void stage_flush(const TraversalParams& P, Stage<kBat
             }
         }
     }
-#pragma unroll
-    for (int h = 0; h < H; ++h) {
-        deg[h] = -1;
-        if (u[h] >= 0) deg[h] = (int)(__ldg(off + u[h] + 1) - __ldg(off + u[h]));
-    }
     if constexpr (kBatch) {
         unsigned long long e = 0;
 #pragma unroll
@@ -329,16 +357,6 @@ __device__ __forceinline__ void stage_flush(const TraversalParams& P, Stage<kBat
             if (u[h] >= 0) e += (unsigned long long)deg[h] * __popcll(S.mask[i0 + h]);
         if (e) atomicAdd(&S.edges, e);
     } else {
-        int32_t cu[H], cv[H];
-#pragma unroll
-        for (int h = 0; h < H; ++h) {
-            cu[h] = u[h];
-            cv[h] = (u[h] >= 0) ? (int32_t)(pv[h] & ~kClaimed) : 0;
-            if (new2old && u[h] >= 0) {
-                cu[h] = __ldg(new2old + u[h]);
-                cv[h] = __ldg(new2old + cv[h]);
-            }
-        }
         // entries whose claim lost are dropped
         int won = 0;
 #pragma unroll
@@ -672,7 +690,7 @@ __device__ void expand_segment_staged(const TraversalParams& P, Stage<false>& S,
         // still in flight (blocks j and j + 1) complete before leaving
         if (lane == 0) {
             raise_status(P, kDevTimeout);
-            atomicExch(&P.stats->abort, 1);
+            give_up(P);
             for (int k = j; k < min(j + 2, nblk); ++k) {
                 const int b = k & 1;
                 const unsigned long long t0 = global_timer_ns();
@@ -1471,10 +1489,12 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
     }
     stamp(P, 0);
     init_plain(P, tid, nthreads);
-    if (grid_barrier(P)) {
+    __shared__ unsigned long long epoch;
+    if (threadIdx.x == 0) epoch = 0ull;
+    if (grid_barrier(P, epoch)) {
         stamp(P, 1);
         seed_plain(P, S);
-        if (grid_barrier(P)) {
+        if (grid_barrier(P, epoch)) {
             stamp(P, 2);
             long long seen_edges = 0;  // edges of all frontiers so far (same in every CTA)
             bool prev_bu = false;
@@ -1492,7 +1512,7 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
                 prepare_level(P, level, dir, tid, nthreads);
                 expand_level<false, kStaged>(P, S, L, level, s_hot, dir);
                 prev_bu = dir == 2;
-                if (!grid_barrier(P)) break;
+                if (!grid_barrier(P, epoch)) break;
                 stamp(P, 3 + level);
             }
         }
@@ -1777,10 +1797,12 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
     const long long tid = (long long)blockIdx.x * kBlock + threadIdx.x;
     stamp(P, 0);
     init_batch(P, tid, nthreads);
-    if (grid_barrier(P)) {
+    __shared__ unsigned long long epoch;
+    if (threadIdx.x == 0) epoch = 0ull;
+    if (grid_barrier(P, epoch)) {
         stamp(P, 1);
         seed_batch(P, S);
-        if (grid_barrier(P)) {
+        if (grid_barrier(P, epoch)) {
             stamp(P, 2);
             bool prev_bu = false;
             for (int level = 0;; ++level) {
@@ -1795,10 +1817,10 @@ bfs_batch_persistent(const __grid_constant__ TraversalParams P) {
                 if (dir == 2 && blockIdx.x == 0 && threadIdx.x == 0) P.stats->bu_levels += 1;
                 expand_level<true>(P, S, L, level, nullptr, dir);
                 prev_bu = dir == 2;
-                if (!grid_barrier(P)) break;
+                if (!grid_barrier(P, epoch)) break;
                 stamp(P, 3 + 2 * level);
                 sweep_batch(P, S, level, tid, nthreads);
-                if (!grid_barrier(P)) break;
+                if (!grid_barrier(P, epoch)) break;
                 stamp(P, 4 + 2 * level);
                 if (blockIdx.x == 0 && threadIdx.x == 0) {
                     if (__ldcg(reinterpret_cast<const unsigned long long*>(

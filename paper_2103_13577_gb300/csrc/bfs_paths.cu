@@ -60,10 +60,10 @@ struct PathCtl {
     unsigned long long packed[2];   // queue of parity p: (entries << 34) | entry prefix
     unsigned long long edges;       // entries of the reached rows
     unsigned long long reached;     // vertices with hops >= 0
-    unsigned int bar_count, bar_gen, exit_count;
+    unsigned long long arrived;     // barrier arrivals of the launch; bit 63: a CTA gave up
+    unsigned int exit_count;
     int bad;                        // a row or column index out of range was met
     int status;                     // 1: a grid-barrier wait gave up
-    int abort;                      // tells waiting CTAs to leave
     int levels;                     // max hops + 1
     int pad;
 };
@@ -95,37 +95,40 @@ __device__ __forceinline__ unsigned long long timer_ns() {
     return t;
 }
 
-// All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA
-// arrives on a counter; the last one bumps a generation word the others
-// poll.  A wait longer than timeout_ns records the failure and makes every
-// CTA leave; the return value says whether to go on.
-__device__ bool path_barrier(const PathParams& P) {
+// All CTAs are co-resident (cooperative launch).  Thread 0 of each CTA adds
+// its arrival to a 64-bit word that only grows during the launch; the k-th
+// barrier is complete once it reaches k * gridDim.x (`epoch`, thread 0's in
+// shared memory, counts the barriers passed, the same in every CTA), so an arrival is one
+// fire-and-forget reduction and the wait a loop of acquire loads.  A wait
+// longer than timeout_ns records the failure and sets bit 63, which makes
+// every CTA leave; the return value says whether to go on.
+constexpr unsigned long long kPathGaveUp = 1ull << 63;
+
+__device__ bool path_barrier(const PathParams& P, unsigned long long& epoch) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        PathCtl* c = P.ctl;
+        unsigned long long* const word = &P.ctl->arrived;
+        const unsigned long long target = ++epoch * gridDim.x;
         int ok = 1;
-        const unsigned g = *(volatile unsigned*)&c->bar_gen;
         __threadfence();
-        if (atomicAdd(&c->bar_count, 1u) + 1u == gridDim.x) {
-            c->bar_count = 0u;
-            __threadfence();
-            atomicExch(&c->bar_gen, g + 1u);
-        } else {
-            const unsigned long long t0 = timer_ns();
-            while (*(volatile unsigned*)&c->bar_gen == g) {
-                if (*(volatile int*)&c->abort) { ok = 0; break; }
-                if (timer_ns() - t0 > (unsigned long long)P.timeout_ns) {
-                    atomicExch(&c->status, 1);
-                    atomicExch(&c->abort, 1);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+        asm volatile("red.relaxed.gpu.global.add.u64 [%0], 1;" ::"l"(word) : "memory");
+        unsigned long long t0 = 0ull;
+        for (;;) {
+            unsigned long long a;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(a) : "l"(word) : "memory");
+            if (a & kPathGaveUp) { ok = 0; break; }
+            if (a >= target) break;
+            const unsigned long long t = timer_ns();
+            if (t0 == 0ull) {
+                t0 = t;
+            } else if (t - t0 > (unsigned long long)P.timeout_ns) {
+                atomicExch(&P.ctl->status, 1);
+                atomicOr(word, kPathGaveUp);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
-        if (*(volatile int*)&c->abort) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
@@ -331,7 +334,9 @@ paths_persistent(const __grid_constant__ PathParams P) {
         P.vis[i] = 0u;
         P.mark[i] = 0u;
     }
-    if (path_barrier(P)) {
+    __shared__ unsigned long long epoch;
+    if (threadIdx.x == 0) epoch = 0ull;
+    if (path_barrier(P, epoch)) {
         if (tid == 0) {
             const int32_t r = P.root;
             P.vis[r >> 5] = 1u << (r & 31);
@@ -349,7 +354,7 @@ paths_persistent(const __grid_constant__ PathParams P) {
             P.ctl->reached = 1;
             P.ctl->levels = 1;
         }
-        bool ok = path_barrier(P);
+        bool ok = path_barrier(P, epoch);
         for (int level = 0; ok; ++level) {
             const int cur = level & 1, nxt = cur ^ 1;
             const unsigned long long pk = __ldcg(&P.ctl->packed[cur]);
@@ -361,9 +366,9 @@ paths_persistent(const __grid_constant__ PathParams P) {
                 P.ctl->packed[nxt] = 0ull;   // last read at the start of level - 1
             }
             expand_paths(P, cur, cnt, E);
-            if (!path_barrier(P)) break;
+            if (!path_barrier(P, epoch)) break;
             collect_paths(P, level, nxt);
-            ok = path_barrier(P);
+            ok = path_barrier(P, epoch);
         }
     }
     // last CTA out resets the barrier state for the next launch
@@ -372,8 +377,7 @@ paths_persistent(const __grid_constant__ PathParams P) {
         __threadfence();
         if (atomicAdd(&P.ctl->exit_count, 1u) + 1u == gridDim.x) {
             P.ctl->exit_count = 0u;
-            P.ctl->bar_count = 0u;
-            P.ctl->abort = 0;
+            P.ctl->arrived = 0ull;
         }
     }
 }
