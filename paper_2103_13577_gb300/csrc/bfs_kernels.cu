@@ -831,26 +831,27 @@ __device__ __forceinline__ unsigned unit_mask(int r, int lo, int hi) {
     return ((1u << b) - 1u) & ~((1u << a) - 1u);
 }
 
-// Bin 1: one warp per chunk of chunk_warp edges.  The chunk's vertex
-// segments (up to 32 at a time) are cut into 16-byte units (4 columns, the
-// first rounded down to a 16-byte boundary) laid end to end by a scan; each
-// round a lane takes two units, finds their segments by a shuffle binary
-// search, and reads each with one 128-bit load -- short and long segments
-// alike keep every lane busy.
+// Bins 1 and 2 as warp items: edges [cs, ce) of bin b's level sequence
+// (a bin-1 chunk of chunk_warp edges, or, on small levels, a 32-edge slice
+// of either bin).  The range's vertex segments (up to 32 at a time, from the
+// entry that holds the first edge of its base chunk) are cut into 16-byte
+// units (4 columns, the first rounded down to a 16-byte boundary) laid end
+// to end by a scan; each round a lane takes two units, finds their segments
+// by a shuffle binary search, and reads each with one 128-bit load -- short
+// and long segments alike keep every lane busy.
 template <bool kBatch>
-__device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, int cur,
-                                  long long item, int k, long long cnt, long long E, int level,
+__device__ void expand_warp_range(const TraversalParams& P, Stage<kBatch>& S, const BinQueue& Q,
+                                  int cshift, long long cs, long long ce, long long cnt, int level,
                                   int nxt, int nslot) {
-    const BinQueue& Q = P.q[cur][1];
     const unsigned lane = lane_id();
-    const long long cs = item * k * (long long)P.chunk_warp;
-    const long long ce = min(cs + k * (long long)P.chunk_warp, E);
-    long long i = __ldcg(Q.chunk + item * k);
+    long long i = __ldcg(Q.chunk + (cs >> cshift));
     for (;;) {
         const long long ij = i + lane;
         long long eo = 0x7fffffffffffffffll;
         if (ij < cnt) eo = __ldcg(Q.eoff + ij);
         const bool ok = eo < ce;
+        bool live = false;  // the segment overlaps [cs, ce) (a slice's first
+                            // entries may end before cs)
         int32_t v = 0;
         long long a = 0, b = 0;
         uint64_t mask = 0ull;
@@ -858,15 +859,16 @@ __device__ void expand_warp_chunk(const TraversalParams& P, Stage<kBatch>& S, in
             v = __ldcg(Q.v + ij);
             const long long base = __ldg(P.off + v), end = __ldg(P.off + v + 1);
             const long long lo = max(eo, cs), hi = min(eo + (end - base), ce);
+            live = hi > lo;
             a = base + (lo - eo);
             b = base + (hi - eo);
             if (kBatch) mask = __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij);
-            if (P.l2_prefetch) prefetch_cols_l2(P.col, a, min(b, a + kPrefetchAhead));
+            if (P.l2_prefetch && live) prefetch_cols_l2(P.col, a, min(b, a + kPrefetchAhead));
         }
         const unsigned okb = __ballot_sync(FULL_MASK, ok);
         const long long a4 = a & ~3ll;
         const int rlo = (int)(a - a4), rhi = (int)(b - a4);  // valid columns, relative to a4
-        const int units = ok ? (rhi + 3) >> 2 : 0;
+        const int units = live ? (rhi + 3) >> 2 : 0;
         const int incl = warp_incl_scan(units);
         const int excl = incl - units;
         const int total = __shfl_sync(FULL_MASK, incl, 31);
@@ -963,8 +965,11 @@ __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int
 
 struct LevelShape {
     long long cnt[kBins], edges[kBins];
-    long long n_cta, chunks_warp, groups_small;  // work items (CTA chunks, warp chunks, groups)
-    int k_cta, k_warp;                           // base chunks per work item
+    long long n_cta;            // CTA items (bin 2)
+    long long items_w1, items_w2;  // warp items of bins 1 and 2
+    long long groups_small;     // light groups (bin 0)
+    int k_cta;                  // base chunks per CTA item
+    int sh_w1, sh_w2;           // log2 of the edges of a warp item of bins 1 and 2
     unsigned discovered;
 };
 
@@ -996,10 +1001,26 @@ __device__ __forceinline__ LevelShape read_level(const TraversalParams& P, int l
     const long long base_warp =
         min((s.edges[1] + P.chunk_warp - 1) >> sh_warp, (long long)P.q[cur][1].chunk_cap);
     s.k_cta = pow2_floor_clamped(base_cta / (4ll * gridDim.x), 32);
-    s.k_warp = pow2_floor_clamped(base_warp / (4ll * gridDim.x * kWarps), 16);
+    const int k_warp = pow2_floor_clamped(base_warp / (4ll * gridDim.x * kWarps), 16);
     s.n_cta = (base_cta + s.k_cta - 1) / s.k_cta;
-    s.chunks_warp = (base_warp + s.k_warp - 1) / s.k_warp;
+    s.items_w1 = (base_warp + k_warp - 1) / k_warp;
+    s.sh_w1 = sh_warp + __ffs(k_warp) - 1;
+    s.items_w2 = 0;
+    s.sh_w2 = sh_cta;
     s.groups_small = (s.cnt[0] + 31) / 32;
+    // Small levels: bins 1 and 2 cut into 32-edge warp slices when that,
+    // with the light groups, still gives no warp more than one item.  The
+    // level then costs one slice's chain of dependent accesses, where a
+    // CTA chunk (1024 edges on 4 warps) or a warp chunk chained a probe
+    // round and several flushes of its discoveries.
+    const long long f1 = min((s.edges[1] + 31) >> 5, base_warp << (sh_warp - 5));
+    const long long f2 = min((s.edges[2] + 31) >> 5, base_cta << (sh_cta - 5));
+    if (f1 + f2 > 0 && f1 + f2 + s.groups_small <= (long long)gridDim.x * kWarps) {
+        s.n_cta = 0;
+        s.items_w1 = f1;
+        s.items_w2 = f2;
+        s.sh_w1 = s.sh_w2 = 5;
+    }
     return s;
 }
 
@@ -1261,19 +1282,25 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
         tiles = ((P.n + 31) / 32 + 31) / 32 - tile0;
     }
     const long long small_items = (!kBatch && bitmap) ? tiles : L.groups_small;
-    const long long witems = L.chunks_warp + small_items;
+    const long long w1 = L.items_w1, w12 = w1 + L.items_w2;
+    const long long witems = w12 + small_items;
+    const int sh_warp = __ffs(P.chunk_warp) - 1, sh_cta = __ffs(P.chunk_cta) - 1;
     for (long long it = gw; it < witems; it += nwarps) {
-        if (it < L.chunks_warp) {
-            expand_warp_chunk<kBatch>(P, S, cur, it, L.k_warp, L.cnt[1], L.edges[1], level, nxt,
-                                      nslot);
+        if (it < w12) {
+            const bool b2 = it >= w1;
+            const int shw = b2 ? L.sh_w2 : L.sh_w1;
+            const long long cs = (b2 ? it - w1 : it) << shw;
+            const long long E = b2 ? L.edges[2] : L.edges[1];
+            expand_warp_range<kBatch>(P, S, P.q[cur][b2 ? 2 : 1], b2 ? sh_cta : sh_warp, cs,
+                                      min(cs + (1ll << shw), E), b2 ? L.cnt[2] : L.cnt[1], level,
+                                      nxt, nslot);
         } else if constexpr (!kBatch) {
             if (bitmap)
-                expand_bitmap_tile(P, S, tile0 + (it - L.chunks_warp), level, nxt, nslot);
+                expand_bitmap_tile(P, S, tile0 + (it - w12), level, nxt, nslot);
             else
-                expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt,
-                                           nslot);
+                expand_small_group<kBatch>(P, S, cur, it - w12, L.cnt[0], level, nxt, nslot);
         } else {
-            expand_small_group<kBatch>(P, S, cur, it - L.chunks_warp, L.cnt[0], level, nxt, nslot);
+            expand_small_group<kBatch>(P, S, cur, it - w12, L.cnt[0], level, nxt, nslot);
         }
     }
 }
