@@ -1632,26 +1632,90 @@ __device__ __forceinline__ void record_lane_level(const TraversalParams& P, int 
 
 // After the last level: dist rows in the caller's numbering, one thread per
 // caller vertex (coalesced stores in every row); unreached lanes get -1.
+// Caller-order rows from the per-vertex level rows.  Four consecutive
+// caller vertices per thread: each lane row gets one 16-byte (int32) or
+// 4-byte (int8) store covering all four, when the row starts keep that
+// alignment (n a multiple of 4, dist 16-byte aligned); otherwise one store
+// per value.  A level byte of 255 marks a lane whose level (>= 255) was
+// written straight into dist: such values are left as they are.
+__device__ __forceinline__ uint32_t level_byte(const uint4& r, int b) {
+    const uint32_t w = b < 4 ? r.x : b < 8 ? r.y : b < 12 ? r.z : r.w;
+    return (w >> (8 * (b & 3))) & 0xffu;
+}
+
 __device__ void emit_batch(const TraversalParams& P, long long tid, long long nthreads) {
+    const bool vec = (P.n & 3) == 0 && ((uintptr_t)P.dist & 15) == 0;
+    if (vec) {
+        const long long groups = P.n >> 2;
+        for (long long g = tid; g < groups; g += nthreads) {
+            const long long c0 = g << 2;
+            uint64_t vis[4];
+            const uint4* lv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const long long v = P.old2new ? __ldg(P.old2new + c0 + j) : c0 + j;
+                vis[j] = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_vn) + 2 * v);
+                lv[j] = reinterpret_cast<const uint4*>(P.lane_level + v * 64);
+            }
+#pragma unroll 1
+            for (int k = 0; k < 4 && 16 * k < P.nlanes; ++k) {
+                uint4 r[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    r[j] = vis[j] ? __ldcg(lv[j] + k) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int b = 0; b < 16; ++b) {
+                    const int i = 16 * k + b;
+                    if (i >= P.nlanes) break;
+                    int val[4];
+                    bool deep = false;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool hit = (vis[j] >> i) & 1ull;
+                        const int lvl = (int)level_byte(r[j], b);
+                        deep |= hit && lvl == 255;
+                        val[j] = hit ? lvl : -1;
+                    }
+                    const long long idx = (long long)i * P.n + c0;
+                    if (!deep) {
+                        if (P.dist_int8)
+                            *reinterpret_cast<uint32_t*>(reinterpret_cast<int8_t*>(P.dist) + idx) =
+                                (uint32_t)(val[0] & 0xff) | ((uint32_t)(val[1] & 0xff) << 8) |
+                                ((uint32_t)(val[2] & 0xff) << 16) | ((uint32_t)(val[3] & 0xff) << 24);
+                        else
+                            *reinterpret_cast<int4*>(P.dist + idx) =
+                                make_int4(val[0], val[1], val[2], val[3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            if (((vis[j] >> i) & 1ull) && val[j] == 255) continue;
+                            if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx + j] = (int8_t)val[j];
+                            else P.dist[idx + j] = val[j];
+                        }
+                    }
+                }
+            }
+        }
+        return;
+    }
     for (long long c = tid; c < P.n; c += nthreads) {
         const long long v = P.old2new ? __ldg(P.old2new + c) : c;
         const uint64_t vis = __ldcg(reinterpret_cast<const unsigned long long*>(P.lane_vn) + 2 * v);
         const uint4* lv = reinterpret_cast<const uint4*>(P.lane_level + v * 64);
-        uint4 q[4] = {make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0), make_uint4(0, 0, 0, 0),
-                      make_uint4(0, 0, 0, 0)};
-        if (vis) {
+        for (int k = 0; k < 4 && 16 * k < P.nlanes; ++k) {
+            const uint4 r = vis ? __ldcg(lv + k) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = __ldcg(lv + k);
-        }
-        const uint8_t* bytes = reinterpret_cast<const uint8_t*>(q);
-        for (int i = 0; i < P.nlanes; ++i) {
-            const bool hit = (vis >> i) & 1ull;
-            const int lvl = bytes[i];
-            if (hit && lvl == 255) continue;  // deep level, already written
-            const int val = hit ? lvl : -1;
-            const long long idx = (long long)i * P.n + c;
-            if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)val;
-            else P.dist[idx] = val;
+            for (int b = 0; b < 16; ++b) {
+                const int i = 16 * k + b;
+                if (i >= P.nlanes) break;
+                const bool hit = (vis >> i) & 1ull;
+                const int lvl = (int)level_byte(r, b);
+                if (hit && lvl == 255) continue;  // deep level, already written
+                const int val = hit ? lvl : -1;
+                const long long idx = (long long)i * P.n + c;
+                if (P.dist_int8) reinterpret_cast<int8_t*>(P.dist)[idx] = (int8_t)val;
+                else P.dist[idx] = val;
+            }
         }
     }
 }

@@ -128,6 +128,27 @@ def test_batch_deep_graph_int32(ctx):
     g.close()
 
 
+@pytest.mark.parametrize("dtype", [torch.int32, torch.int8])
+def test_batch_row_layouts(ctx, dtype):
+    # the result rows are written four vertices per store when every row
+    # start is aligned (n a multiple of 4, rows 16-byte aligned) and one
+    # value per store otherwise: n = 702 and rows starting one element
+    # past an aligned address take the second form
+    for off, col in (G.grid(27, 26), graphgen.kronecker(10, 8, seed=5)):
+        n = len(off) - 1
+        roots = graphgen.pick_roots(off, 9, seed=7)
+        ref, _ = expected(off, col, roots)
+        g = bfs.Graph(ctx, off, col)
+        flat = torch.empty(len(roots) * n + 1, dtype=dtype, device="cuda")
+        rows = flat[1:].view(len(roots), n)
+        g.run_batch(roots, rows)
+        g.batch_sync()
+        assert np.array_equal(rows.cpu().numpy().astype(np.int32), ref)
+        aligned, _ = batch_gpu(g, n, roots, dtype=dtype)
+        assert np.array_equal(aligned.astype(np.int32), ref)
+        g.close()
+
+
 def test_batch_equals_plain_runs(ctx):
     off, col = graphgen.erdos_renyi(13, 16, seed=8)
     n = len(off) - 1
