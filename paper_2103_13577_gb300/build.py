@@ -1,6 +1,6 @@
 """Builds libbfs.so in-tree with nvcc for sm_103a (GB300).
 
-Nine translation units compiled in parallel and linked into one shared
+Ten translation units compiled in parallel and linked into one shared
 library with the static CUDA runtime.  No cmake, no torch extension
 machinery: the library is plain C ABI (include/bfs.h).
 """
@@ -15,8 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbfs.so")
-SOURCES = ["bfs_kernels.cu", "bfs_capi.cu", "bfs_server.cpp", "bfs_static.cu", "bfs_relabel.cu",
-           "bfs_tune.cpp", "bfs_butterfly.cu", "bfs_lrb.cu", "bfs_paths.cu"]
+SOURCES = ["bfs_kernels.cu", "bfs_kernels_lean.cu", "bfs_capi.cu", "bfs_server.cpp",
+           "bfs_static.cu", "bfs_relabel.cu", "bfs_tune.cpp", "bfs_butterfly.cu", "bfs_lrb.cu",
+           "bfs_paths.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
               "-I", os.path.join(os.path.dirname(HERE), "include")]

@@ -15,6 +15,9 @@ namespace bfs {
 
 // kernels and launch helpers (bfs_kernels.cu)
 const void* plain_persistent_fn(int mb, bool staged = false);
+namespace lean {
+const void* plain_persistent_fn(int mb);
+}
 const void* plain_step_fn(int mb, bool staged = false);
 const void* batch_persistent_fn(int mb);
 const void* batch_step_fn(int mb);
@@ -302,6 +305,20 @@ static bfs_status grid_size(bfs_graph* g, const void* fn, int32_t* out, size_t s
     return BFS_OK;
 }
 
+// The persistent single-source kernel a traversal of g launches: the lean
+// build (bfs_kernels_lean.cu) whenever the run asks for none of the paths
+// compiled out of it, else the full one.  Both have the same launch bounds
+// and shared memory, and the lean one never uses more registers, so the
+// full kernel's resident grid is resident for either.
+static bool plain_is_lean(const bfs_graph* g) {
+    return g->tma_stage == 0 && g->dir_mode == 0 && g->bitmap_div == 0 && g->hot_words == 0 &&
+           g->use_match_any == 0 && g->l2_prefetch == 0;
+}
+static const void* persistent_plain_fn(const bfs_graph* g) {
+    return plain_is_lean(g) ? lean::plain_persistent_fn(g->min_blocks)
+                            : plain_persistent_fn(g->min_blocks, g->tma_stage != 0);
+}
+
 // Plain-kernel grids for the graph's shared-memory setting (both the
 // persistent kernel and the host-loop step kernel take the same size).
 static bfs_status set_plain_grids(bfs_graph* g) {
@@ -475,8 +492,7 @@ bfs_status run_plain_on(bfs_graph* g, Workspace* ws, int32_t root, int32_t* dist
         return launch_graph_loop(g->loop_plain, P, plain_step_fn(g->min_blocks, g->tma_stage != 0),
                                  false, grid > 0 ? grid : g->grid_plain, smem, s);
     if (!(flags & BFS_HOST_LOOP))
-        return launch_coop(plain_persistent_fn(g->min_blocks, g->tma_stage != 0),
-                           grid > 0 ? grid : g->grid_plain, P, s, smem);
+        return launch_coop(persistent_plain_fn(g), grid > 0 ? grid : g->grid_plain, P, s, smem);
     // host-driven level loop: init, seed, then one launch per level
     bfs_status st;
     const void* fn = plain_step_fn(g->min_blocks, g->tma_stage != 0);
@@ -578,8 +594,7 @@ bfs_status batch_finish(bfs_graph* g, Workspace* ws, cudaStream_t s, bfs_run_sta
 int32_t plain_grid_of(const bfs_graph* g) { return g->grid_plain; }
 
 bfs_status cta_footprint(const bfs_graph* g, bool batched, CtaFootprint* out) {
-    const void* fn = batched ? batch_persistent_fn(g->min_blocks)
-                             : plain_persistent_fn(g->min_blocks, g->tma_stage != 0);
+    const void* fn = batched ? batch_persistent_fn(g->min_blocks) : persistent_plain_fn(g);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");

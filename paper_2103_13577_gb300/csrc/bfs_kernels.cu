@@ -37,7 +37,26 @@
 
 #include "bfs_internal.h"
 
+// This file is compiled twice.  As is, it holds every traversal kernel and
+// the upload helpers.  bfs_kernels_lean.cu compiles it again with
+// BFS_LEAN_PATHS = 1 into namespace bfs::lean, where only the single-source
+// persistent kernel is instantiated and the paths that the full kernel
+// enables at run time -- direction optimisation and the frontier bitmaps,
+// the shared-memory copy of the hot bitmap, warp-aggregated claims, bulk L2
+// prefetch -- are compiled out.  The host launches that kernel whenever a
+// traversal uses none of them (the default): its probe loops then get the
+// registers those paths held (spills at 4 CTAs/SM 232/352 -> 108/256 bytes,
+// 0.539 -> 0.493 ms per scale-22 root).
+#ifndef BFS_LEAN_PATHS
+#define BFS_LEAN_PATHS 0
+#endif
+
 namespace bfs {
+#if BFS_LEAN_PATHS
+namespace lean {
+#endif
+
+constexpr bool kLean = BFS_LEAN_PATHS != 0;
 
 #define FULL_MASK 0xffffffffu
 
@@ -283,7 +302,7 @@ __device__ __forceinline__ void stage_flush(const TraversalParams& P, Stage<kBat
     const int32_t* const new2old = P.new2old;
     int32_t* const dist = P.dist;
     int32_t* const parent = P.parent;
-    uint32_t* const fbn = P.fb[0] ? P.fb[(level + 1) % 3] : nullptr;
+    uint32_t* const fbn = (!kLean && P.fb[0]) ? P.fb[(level + 1) % 3] : nullptr;
     const int t_small = P.t_small, t_large = P.t_large;
     const int sh_warp = __ffs(P.chunk_warp) - 1, sh_cta = __ffs(P.chunk_cta) - 1;
     unsigned long long* const packed = P.ctl[nslot].packed;
@@ -321,7 +340,7 @@ __device__ __forceinline__ void stage_flush(const TraversalParams& P, Stage<kBat
                 cv[h] = __ldg(new2old + cv[h]);
             }
         }
-        if (P.use_match_any) {
+        if (!kLean && P.use_match_any) {
             // lanes claiming bits of the same word merge them: one atomicOr
             // per word, the first lane holding a vertex wins it
 #pragma unroll
@@ -564,7 +583,7 @@ __device__ __forceinline__ void visit_plain_k(const TraversalParams& P, Stage<fa
     // pass 1 (shared memory only): drop edges whose target was visited before
     // the level and lies in the hot prefix copied at level start
     const int hot_bits = S.hot_bits;
-    if (hot_bits > 0) {
+    if (!kLean && hot_bits > 0) {
         const uint32_t* hot = S.hot;
 #pragma unroll
         for (int j = 0; j < K; ++j)
@@ -749,7 +768,7 @@ __device__ __forceinline__ void expand_segment(const TraversalParams& P, Stage<k
         return;
     }
     for (int rw = (int)wbase; rw < hi; rw += (int)wstride) {
-        if (P.l2_prefetch && lane == 0 && rw + kPrefetchAhead < hi)
+        if (!kLean && P.l2_prefetch && lane == 0 && rw + kPrefetchAhead < hi)
             prefetch_cols_l2(P.col, a4 + rw + kPrefetchAhead,
                              a4 + min((long long)hi, rw + kPrefetchAhead + 256));
         const int r0 = rw + 4 * (int)lane;
@@ -863,7 +882,7 @@ __device__ void expand_warp_range(const TraversalParams& P, Stage<kBatch>& S, co
             a = base + (lo - eo);
             b = base + (hi - eo);
             if (kBatch) mask = __ldcg(reinterpret_cast<const unsigned long long*>(Q.mask) + ij);
-            if (P.l2_prefetch && live) prefetch_cols_l2(P.col, a, min(b, a + kPrefetchAhead));
+            if (!kLean && P.l2_prefetch && live) prefetch_cols_l2(P.col, a, min(b, a + kPrefetchAhead));
         }
         const unsigned okb = __ballot_sync(FULL_MASK, ok);
         const long long a4 = a & ~3ll;
@@ -940,7 +959,7 @@ __device__ void expand_cta_chunk(const TraversalParams& P, Stage<kBatch>& S, int
             const long long base = __ldg(P.off + v), end = __ldg(P.off + v + 1);
             s_base[threadIdx.x] = base;
             s_end[threadIdx.x] = end;
-            if (P.l2_prefetch) {
+            if (!kLean && P.l2_prefetch) {
                 const long long a = base + (max(eo, cs) - eo);
                 const long long b = base + (min(eo + (end - base), ce) - eo);
                 prefetch_cols_l2(P.col, a, min(b, a + kPrefetchAhead));
@@ -1277,11 +1296,11 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
     // bitmap mode: the light bin's groups are replaced by bitmap tiles
     // starting at the first tile that can hold a light vertex
     long long tile0 = 0, tiles = 0;
-    if (!kBatch && bitmap) {
+    if (!kLean && !kBatch && bitmap) {
         tile0 = P.bitmap_from / 1024;
         tiles = ((P.n + 31) / 32 + 31) / 32 - tile0;
     }
-    const long long small_items = (!kBatch && bitmap) ? tiles : L.groups_small;
+    const long long small_items = (!kLean && !kBatch && bitmap) ? tiles : L.groups_small;
     const long long w1 = L.items_w1, w12 = w1 + L.items_w2;
     const long long witems = w12 + small_items;
     const int sh_warp = __ffs(P.chunk_warp) - 1, sh_cta = __ffs(P.chunk_cta) - 1;
@@ -1295,7 +1314,7 @@ __device__ void expand_top_down(const TraversalParams& P, Stage<kBatch>& S, cons
                                       min(cs + (1ll << shw), E), b2 ? L.cnt[2] : L.cnt[1], level,
                                       nxt, nslot);
         } else if constexpr (!kBatch) {
-            if (bitmap)
+            if (!kLean && bitmap)
                 expand_bitmap_tile(P, S, tile0 + (it - w12), level, nxt, nslot);
             else
                 expand_small_group<kBatch>(P, S, cur, it - w12, L.cnt[0], level, nxt, nslot);
@@ -1318,7 +1337,7 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
         // degree-ordered renumbering, the highest-degree vertices) into
         // shared memory; most probes of a dense level end there
         const long long ledges = L.edges[0] + L.edges[1] + L.edges[2];
-        const int words = (P.hot_words > 0 && ledges >= P.hot_min_edges)
+        const int words = (!kLean && P.hot_words > 0 && ledges >= P.hot_min_edges)
                               ? (int)min((long long)P.hot_words, (long long)((P.n + 31) / 32)) : 0;
         if (words > 0) {
             const int w4 = words / 4;
@@ -1334,7 +1353,7 @@ __device__ void expand_level(const TraversalParams& P, Stage<kBatch>& S, const L
     }
     __syncthreads();
     bool bottom_up = false;
-    if (dir == 2) {
+    if (!kLean && dir == 2) {
         if constexpr (kBatch) bottom_up_batch_level(P, level);
         else bottom_up_level(P, S, level, nxt, nslot);
         bottom_up = true;
@@ -1385,7 +1404,7 @@ __device__ void init_plain(const TraversalParams& P, long long tid, long long nt
     }
     const long long words = (P.n + 31) / 32;
     fill_bytes(P.visited, words * 4, 0, tid, nthreads);
-    if (P.fb[0])
+    if (!kLean && P.fb[0])
         for (int f = 0; f < 3; ++f) fill_bytes(P.fb[f], words * 4, 0, tid, nthreads);
     fill_bytes(P.dist, P.n * 4, 0xff, tid, nthreads);
     if (P.parent) fill_bytes(P.parent, P.n * 4, 0xff, tid, nthreads);
@@ -1407,7 +1426,7 @@ __device__ void seed_plain(const TraversalParams& P, Stage<false>& S) {
 // bottom-up levels are counted.
 __device__ void prepare_level(const TraversalParams& P, int level, int dir, long long tid,
                               long long nthreads) {
-    if (!P.fb[0]) return;
+    if (kLean || !P.fb[0]) return;
     fill_bytes(P.fb[(level + 2) % 3], ((P.n + 31) / 32) * 4, 0, tid, nthreads);
     if (dir == 2 && blockIdx.x == 0 && threadIdx.x == 0) P.stats->bu_levels += 1;
 }
@@ -1532,7 +1551,7 @@ bfs_plain_persistent(const __grid_constant__ TraversalParams P) {
                 if (nf == 0) break;
                 const long long mf = L.edges[0] + L.edges[1] + L.edges[2];
                 seen_edges += mf;
-                const int dir = P.fb[0] ? choose_direction(P.dir_mode, prev_bu, mf, P.nnz - seen_edges,
+                const int dir = (!kLean && P.fb[0]) ? choose_direction(P.dir_mode, prev_bu, mf, P.nnz - seen_edges,
                                                            nf, P.n, P.do_alpha, P.do_beta,
                                                            P.bitmap_div)
                                         : 0;
@@ -1967,6 +1986,14 @@ bfs_batch_step(const __grid_constant__ TraversalParams P) {
     }
 }
 
+#if BFS_LEAN_PATHS
+// The lean build's one kernel family (see the top of the file).
+const void* plain_persistent_fn(int mb) {
+    return mb >= 4 ? (const void*)bfs_plain_persistent<4, false>
+         : mb == 3 ? (const void*)bfs_plain_persistent<3, false>
+                   : (const void*)bfs_plain_persistent<2, false>;
+}
+#else
 // ------------------------------------------------------ upload helpers
 // CSR validation: flags[0] |= 1 for a column out of range, |= 2 for a
 // decreasing offset.
@@ -2132,4 +2159,9 @@ cudaError_t launch_degree_bins(const int64_t* off, long long n, int t_small, int
     return cudaGetLastError();
 }
 
+#endif  // BFS_LEAN_PATHS
+
+#if BFS_LEAN_PATHS
+}  // namespace lean
+#endif
 }  // namespace bfs

@@ -23,7 +23,9 @@
 
 namespace bfs {
 
-const void* plain_persistent_fn(int mb, bool staged = false);
+namespace lean {
+const void* plain_persistent_fn(int mb);
+}
 
 namespace {
 
@@ -76,7 +78,7 @@ cudaError_t setup_device(StaticDevice& d, int dev) {
     int sms = 0, nb = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, plain_persistent_fn(2), kBlock, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lean::plain_persistent_fn(2), kBlock, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return e;
@@ -208,7 +210,7 @@ extern "C" bfs_status bfs_run_static(const int64_t* row_off, const int32_t* col,
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: CSR check launch");
     void* args[] = {&P};
-    e = cudaLaunchCooperativeKernel(plain_persistent_fn(2), dim3(d.grid), dim3(kBlock), args, 0, s);
+    e = cudaLaunchCooperativeKernel(lean::plain_persistent_fn(2), dim3(d.grid), dim3(kBlock), args, 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "bfs_run_static: cooperative launch");
     if (!stats) return BFS_OK;
     DevStats h;
