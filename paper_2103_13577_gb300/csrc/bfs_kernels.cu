@@ -828,15 +828,21 @@ __device__ void expand_small_group(const TraversalParams& P, Stage<kBatch>& S, i
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int e = e0 + 32 * j + (int)lane;
-            const int o = e < total ? own[32 * j + lane] : 0;
-            const long long bo = __shfl_sync(FULL_MASK, base, o);
-            const int xo = __shfl_sync(FULL_MASK, excl, o);
-            vv[j] = __shfl_sync(FULL_MASK, v, o);
-            mm[j] = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, o) : 0ull;
             u[j] = 0;
-            if (e < total) {
-                okm |= 1u << j;
-                u[j] = __ldcs(P.col + bo + (e - xo));
+            vv[j] = 0;
+            mm[j] = 0ull;
+            // slots past the round's last edge (the same for the whole warp)
+            // need no owner lookup
+            if (e0 + 32 * j < total) {
+                const int o = e < total ? own[32 * j + lane] : 0;
+                const long long bo = __shfl_sync(FULL_MASK, base, o);
+                const int xo = __shfl_sync(FULL_MASK, excl, o);
+                vv[j] = __shfl_sync(FULL_MASK, v, o);
+                mm[j] = kBatch ? __shfl_sync(FULL_MASK, (unsigned long long)mask, o) : 0ull;
+                if (e < total) {
+                    okm |= 1u << j;
+                    u[j] = __ldcs(P.col + bo + (e - xo));
+                }
             }
         }
         visit_k<kBatch, 8>(P, S, okm, u, vv, mm, level, nxt, nslot);
