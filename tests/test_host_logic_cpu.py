@@ -77,3 +77,23 @@ def test_batch_frontier_sums_unreached_and_isolated():
     deg = torch.tensor([1, 0, 1], dtype=torch.int64)
     sizes, degs, reached = bench.batch_frontier_sums(rows, deg)
     assert sizes == [2, 2] and degs == [2, 2] and reached == 2
+
+
+def test_traffic_records_follow_the_kernel_sources(tmp_path):
+    # the bench reports a committed ncu traffic figure only while the kernel
+    # source it was captured on is unchanged
+    changed = tmp_path / "kernel.cu"
+    changed.write_bytes(open(bench.KERNEL_SRC, "rb").read() + b"\n// changed\n")
+    assert bench.recorded_traffic(bench.TRAFFIC_FILE, str(changed)) is None
+    assert bench.recorded_traffic(str(tmp_path / "missing.json")) is None
+    stale = []
+    for rec, src in ((bench.TRAFFIC_FILE, bench.KERNEL_SRC),
+                     (bench.BATCH_TRAFFIC_FILE, bench.KERNEL_SRC),
+                     (bench.PATHS_TRAFFIC_FILE, bench.PATHS_SRC)):
+        value = bench.recorded_traffic(rec, src)
+        if value is None:
+            stale.append(os.path.basename(rec))
+        else:
+            assert value > 0
+    if stale:
+        pytest.skip("captured on an earlier kernel source (re-profile on a GPU): " + ", ".join(stale))
